@@ -1,0 +1,367 @@
+"""Benchmark of the GB300 WCSPH hot path.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+A step is one pass of the whole hot path: neighbour pipeline (hash, sort,
+reorder, cell start/end, split neighbour list), forces at n + predictor,
+forces at the predicted state + corrector, CFL dt.  The default workload is
+the ~1M-fluid-particle 3D dam break (tank 1.6 x 0.67 x 0.6 m, column
+0.4 x 0.67 x 0.3 m, dp = 4.3 mm, 3 layers of dynamic boundary particles,
+1.65M particles in total), synthetic and seeded; its arrays (~1.3 GB with
+the neighbour list) exceed the 126 MB L2, so no flush is needed between
+steps.
+
+Metric: particle-interactions/s = (neighbour-list entries of each step's
+build x 2 force passes) / time; particle-steps/s is reported beside it.
+Rank 0 prints one JSON line.  Under torchrun each rank runs an independent
+replica (the single scene does not shard; "replicas only") and value is the
+whole-job aggregate over the max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-interactions/s and particle-steps/s at 1 GB300, % HBM roofline"
+UNIT = "particle-interactions/s"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+
+def make_workload(name):
+    from paper_2207_11328_gb300 import scenes
+    if name == "dam1m":
+        return scenes.dam_break(dp=4.3e-3), "dam_break_1M: tank 1.6x0.67x0.6 m, column 0.4x0.67x0.3 m, dp 4.3 mm"
+    if name == "dam16m":
+        return (scenes.dam_break(dp=4.3e-3 / 16 ** (1 / 3)),
+                "dam_break_16M: tank 1.6x0.67x0.6 m, column 0.4x0.67x0.3 m, dp 1.71 mm")
+    if name == "box":
+        return scenes.periodic_box(n_per_axis=16), "periodic_box_4096: 16^3 lattice, dp 0.02 m"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        load = sorted(sm)[len(sm) // 2:] if sm else []   # upper half: samples under load
+        return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(world, v):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# oracle timing (the CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_window(scene, target_n):
+    """Bounded sample of a workload: the particles in the corner cube
+    x, y, z < w of the tank (fluid and walls alike), w chosen so that about
+    target_n particles fall inside."""
+    from paper_2207_11328_gb300 import scenes
+    if target_n >= scene.n:
+        return scene, None
+    lo, hi = 0.0, float(np.max(scene.pos) + 1.0)
+    for _ in range(60):
+        w = 0.5 * (lo + hi)
+        k = int(np.count_nonzero(np.all(scene.pos < w, axis=1)))
+        lo, hi = (w, hi) if k < target_n else (lo, w)
+    mask = np.all(scene.pos < hi, axis=1)
+    return scenes.subset(scene, mask, name=scene.name + f"_corner{hi:.4f}"), hi
+
+
+def interactions_of(p, sub, x):
+    """Pairs a step evaluates twice: all neighbours of fluid particles, fluid
+    neighbours of boundary particles (boundary-boundary pairs carry nothing)."""
+    import oracle
+    off, idx = oracle.neighbors(p, x)
+    per = np.repeat(np.arange(sub.n), np.diff(off))
+    keep = (sub.ptype[per] == 0) | (sub.ptype[idx] == 0)
+    return int(np.count_nonzero(keep))
+
+
+def time_oracle_steps(sub, steps, warmup=0):
+    """The FP64 oracle as it stands, single-threaded, on a bounded sample:
+    warm-up steps untimed, then `steps` predictor-corrector steps timed.
+    Returns (interactions, particle_steps, seconds)."""
+    import oracle
+    p = oracle.params(sub)
+    x, u, d = sub.pos, sub.vel.astype(np.float64), sub.delta.astype(np.float64)
+    a, _ = oracle.rhs(p, x, u, d, sub.mass, sub.ptype)
+    dt = oracle.cfl_dt(p, a, sub.ptype)
+    if warmup:
+        x, u, d, dt, _ = oracle.step(p, x, u, d, sub.mass, sub.ptype, warmup, dt)
+    inter = 0
+    t = 0.0
+    for _ in range(steps):
+        inter += 2 * interactions_of(p, sub, x)      # untimed: the pairs this step will use
+        t0 = time.perf_counter()
+        x, u, d, dt, _ = oracle.step(p, x, u, d, sub.mass, sub.ptype, 1, dt)
+        t += time.perf_counter() - t0
+    return inter, sub.n * steps, t
+
+
+def cpu_baseline(scene, workload, target_n=600_000):
+    sub, w = oracle_window(scene, target_n)
+    inter, psteps, t = time_oracle_steps(sub, 1)
+    where = f"the corner cube x, y, z < {w:.4f} m" if w is not None else "all particles"
+    return {"value": inter / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "particle_steps_per_s": psteps / t,
+            "sample": f"1 predictor-corrector step (neighbour search + 2 force passes + dt) of the FP64 "
+                      f"oracle, single thread, on the {sub.n} particles of the workload in {where} "
+                      f"({inter} interactions, {t:.1f} s)"}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    scene, wdesc = make_workload(args.workload)
+    # size the sample so the whole --steps/--warmup run stays within a few minutes
+    budget = 150.0 / max(1, args.steps + args.warmup)
+    probe, _ = oracle_window(scene, 20_000)
+    _, pn, pt = time_oracle_steps(probe, 1)
+    rate = pn / max(pt, 1e-9)                     # particle-steps/s of the oracle
+    sub, w = oracle_window(scene, max(2000, int(rate * budget)))
+    where = f"the corner cube x, y, z < {w:.4f} m of the workload" if w is not None else "the whole workload"
+    inter, psteps, t = time_oracle_steps(sub, args.steps, args.warmup)
+    value = inter / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": wdesc, "n_particles": scene.n},
+            "particle_steps_per_s": psteps / t,
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": f"each step: one FP64 oracle step (single thread) on the {sub.n} particles "
+                                       f"of {where}"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_2207_11328_gb300 import Simulation, _build
+
+    if rank == 0 or not os.path.exists(_build.LIB):
+        _build.build()
+    barrier(world)
+    scene, wdesc = make_workload(args.workload)
+    stream = torch.cuda.current_stream()
+    sim = Simulation.from_scene(scene, max_neibs=args.max_neibs, stream=stream)
+    sim.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    st0 = sim.stats(stream=stream)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        sim.step(args.steps, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    st1 = sim.stats(stream=stream)
+    entries = st1["list_entries"] - st0["list_entries"]
+    inter_local = 2.0 * entries
+    psteps_local = float(st1["n_active"]) * args.steps
+    t_max = allmax(world, ms) / 1e3
+    value = allsum(world, inter_local) / t_max
+    psteps = allsum(world, psteps_local) / t_max
+    kernels = st1["kernels_per_step"]
+
+    # per-kernel durations (same work, launched one by one with events on the launch stream)
+    phases = sim.step_profiled(args.profile_steps, stream=stream)
+    st2 = sim.stats(stream=stream)
+    n = float(st2["n_active"])
+    e_step = (st2["list_entries"] - st1["list_entries"]) / args.profile_steps
+    hbm, peak_src = load_peaks()
+    # algorithmic bytes per launch (neighbour gathers served by L1/L2 by construction of the sort):
+    #   forces+predictor: read pos4 16 + vel4 16 + scene 4 + count 4 + list 4/entry; write pos*, vel* 32
+    #   forces+corrector: the same reads of the predicted state + list, read and write pos4, vel4 (64)
+    b_pred = n * 72 + 4 * e_step
+    b_corr = n * 104 + 4 * e_step
+    t_pred = phases["forces_predict"] / args.profile_steps / 1e3
+    t_corr = phases["forces_correct"] / args.profile_steps / 1e3
+    achieved = (b_pred + b_corr) / (t_pred + t_corr) / 1e9
+    traffic = None
+    tr_path = os.path.join(ROOT, "profiles", "forces_traffic.json")
+    if os.path.exists(tr_path):
+        try:
+            with open(tr_path) as f:
+                tr = json.load(f)
+            if tr.get("workload") == args.workload:
+                traffic = tr.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": "forces (predictor + corrector passes)", "achieved": achieved,
+                "peak": hbm, "peak_source": f"{peak_src} HBM copy bandwidth", "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": traffic,
+                "algorithmic_bytes_per_step": b_pred + b_corr,
+                "phase_ms_per_step": {k: v / args.profile_steps for k, v in phases.items()}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wdesc, "n_particles": scene.n, "n_fluid": scene.n_fluid, "dp": scene.dp,
+                       "h": scene.h, "max_neibs": args.max_neibs, "rebuild": "every step",
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+            "particle_steps_per_s": psteps, "mean_neighbours": entries / max(1.0, psteps_local),
+            "roofline": roofline, "gpu_launches": int(kernels * args.steps),
+            "clocks": clk.summary()}
+
+    # end to end through the public API with host buffers (upload, one step, download)
+    if args.e2e_steps > 0:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
+        hp = {k: pin(v) for k, v in dict(pos=scene.pos, vel=scene.vel, delta=scene.delta.astype(np.float32),
+                                          mass=scene.mass, ptype=scene.ptype).items()}
+        out = {"pos": pin(np.empty_like(scene.pos)), "vel": pin(np.empty_like(scene.vel)),
+               "delta": pin(np.empty(scene.n, np.float32))}
+        h2d = sum(v.nbytes for v in hp.values())
+        d2h = sum(v.nbytes for v in out.values())
+        inter = 0.0
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.upload(pos=hp["pos"], vel=hp["vel"], delta=hp["delta"], mass=hp["mass"], ptype=hp["ptype"],
+                       stream=stream)
+            e_up = sim.stats(stream=stream, check=False)["list_entries"]
+            sim.step(1, stream=stream)
+            sim.download(stream=stream, out=(out["pos"], out["vel"], out["delta"]))
+            inter += 2.0 * (sim.stats(stream=stream, check=False)["list_entries"] - e_up)
+        torch.cuda.synchronize()
+        t_e2e = allmax(world, time.perf_counter() - t0)
+        line["e2e"] = {"value": allsum(world, inter) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+                       "note": "per step: sph_upload from pinned host arrays (incl. its sort, neighbour "
+                               "build and dt0 forces), sph_step(1), sph_download to pinned host arrays"}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(scene, args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box"])
+    ap.add_argument("--max-neibs", type=int, default=128)
+    ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        # the oracle on the host cores: rank 0 only, no GPU work
+        rank = int(os.environ.get("RANK", "0"))
+        run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)
+        return
+    world, rank, local = dist_setup(args.gpus)
+    run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

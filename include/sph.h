@@ -1,0 +1,211 @@
+/*
+ * sph.h - C ABI of the GB300 weakly-compressible SPH hot path.
+ *
+ * The library runs, on one sm_103a GPU, the per-step pipeline of a
+ * weakly-compressible SPH solver (arXiv 2207.11328, Sections 2.1-2.3):
+ * cell hash -> key sort -> particle reorder -> cell start/end tables ->
+ * split neighbour list -> particle interactions (continuity, momentum with
+ * the Tait/Cole equation of state, Wendland C2 gradient, artificial or
+ * laminar viscosity, dynamic boundary particles) -> predictor-corrector
+ * integration with the CFL time-step reduction.
+ *
+ * Conventions
+ *  - Every call returns SPH_OK (0) or a negative SPH_ERR_* code.  Device
+ *    errors found by kernels (neighbour overflow, non-finite state) are
+ *    recorded in a sticky device error word; they are reported by the next
+ *    call that synchronises (sph_get_stats, sph_download*, sph_sync) and
+ *    stay set until sph_clear_error.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous on that stream unless stated.
+ *  - Host arrays are read or written during the call only (copied);
+ *    pointers named *_dev are device pointers that the caller owns.
+ *  - Particle arrays are particle-major: pos[3*i + axis].
+ *  - The library allocates all its device buffers once, in sph_create, for
+ *    max_particles particles (paper, "The GPU in GPUSPH": arrays are
+ *    allocated once; particles that leave the domain are dropped during the
+ *    sort; a capacity overflow is an error, not a reallocation).
+ */
+#ifndef SPH_GB300_H
+#define SPH_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define SPH_OK                  0
+#define SPH_ERR_ARG            -1  /* bad argument (NULL, size, layout, physics out of range) */
+#define SPH_ERR_CUDA           -2  /* CUDA runtime error (allocation, launch) */
+#define SPH_ERR_CAPACITY       -3  /* more particles than max_particles */
+#define SPH_ERR_NEIB_OVERFLOW  -4  /* a particle has more neighbours than max_neibs (list truncated) */
+#define SPH_ERR_OUT_OF_DOMAIN  -5  /* uploaded particle outside its scene's domain */
+#define SPH_ERR_NONFINITE      -6  /* non-finite value in the uploaded or integrated state */
+#define SPH_ERR_TIMEOUT        -7  /* a bounded device wait gave up */
+#define SPH_ERR_STATE          -8  /* call out of order (e.g. step before upload) */
+
+/* device error word bits (sph_stats.error_bits) */
+#define SPH_EBIT_NEIB_OVERFLOW  1u
+#define SPH_EBIT_NONFINITE      2u
+#define SPH_EBIT_TIMEOUT        4u
+
+/* viscosity models (paper Table 1 "viscous model", Section 2.1) */
+#define SPH_VISC_ARTIFICIAL     0  /* Monaghan artificial viscosity Pi_ij inside the pressure bracket */
+#define SPH_VISC_LAMINAR        1  /* Morris laminar term, kinematic viscosity, harmonic mean */
+
+/* particle types (paper Section 4, split neighbour list: fluid and boundary) */
+#define SPH_FLUID               0
+#define SPH_BOUNDARY            1  /* dynamic boundary particle: fixed, continuity + EOS only */
+
+typedef struct sph_ctx sph_ctx;  /* opaque; owned by the library */
+
+/* Run parameters, copied by sph_create.  All lengths in metres, SI units. */
+typedef struct {
+    double   dp;             /* particle spacing (informative) */
+    double   h;              /* smoothing length */
+    double   kernel_radius;  /* influence radius = kernel_radius*h; Wendland C2 needs 2 */
+    double   rho0;           /* rest density */
+    double   c0;             /* sound speed of scene 0 (per-scene values: sph_set_scenes) */
+    double   gamma;          /* EOS exponent: an integer in [1, 8] */
+    int32_t  visc_model;     /* SPH_VISC_* */
+    int32_t  pad0;
+    double   alpha;          /* artificial-viscosity coefficient */
+    double   nu;             /* kinematic viscosity (laminar) */
+    double   g[3];           /* body force per unit mass on fluid particles */
+    double   cfl;            /* CFL factor of the adaptive time step */
+    double   dt_fixed;       /* > 0: constant time step; <= 0: adaptive (CFL) */
+    double   origin[3];      /* domain of scene 0 */
+    double   size[3];
+    uint32_t periodic_mask;  /* bit0 x, bit1 y, bit2 z; a periodic axis needs >= 3 cells */
+    uint32_t max_particles;  /* capacity, <= 2^26 */
+    uint32_t max_neibs;      /* neighbour-list slots per particle, 8..1024 */
+    uint32_t n_scenes;       /* 1, or the number of scenes given to sph_set_scenes */
+} sph_params;
+
+/* One independent scene of a batch: its own domain, grid and sound speed. */
+typedef struct {
+    double   origin[3];
+    double   size[3];
+    uint32_t periodic_mask;
+    uint32_t pad0;
+    double   c0;
+} sph_scene;
+
+/* Counters read back from the device (sph_get_stats synchronises). */
+typedef struct {
+    uint32_t n_active;        /* particles in the domain (after the last sort) */
+    uint32_t n_removed;       /* particles dropped because they left the domain (cumulative) */
+    uint32_t max_neibs_seen;  /* largest neighbour count found by the last build (before truncation) */
+    uint32_t error_bits;      /* SPH_EBIT_* (sticky) */
+    uint64_t steps;           /* steps taken since upload */
+    double   dt;              /* time step of scene 0 for the next step */
+    double   time;            /* simulated time of scene 0 */
+    uint32_t n_cells;         /* cells over all scenes */
+    uint32_t kernels_per_step;/* kernel launches in one captured step (0 before the first step) */
+    uint64_t list_entries;    /* neighbour-list entries written by all builds since upload;
+                                 each step's two force passes read its build's entries twice */
+} sph_stats;
+
+/* Create a context on the current CUDA device and allocate every device
+ * buffer for p->max_particles particles.  The grid of scene 0 comes from
+ * p->origin/size/periodic_mask with cell side size/floor(size/(kernel_radius*h))
+ * (>= the influence radius, paper Section 2.3).  Returns SPH_ERR_ARG for
+ * invalid physics or sizes, SPH_ERR_CUDA if allocation fails; *out is set
+ * only on success. */
+int sph_create(const sph_params* p, sph_ctx** out);
+
+/* Replace the scene table by n_scenes independent scenes (batched stepping).
+ * Must precede sph_upload; reallocates the cell tables (host call, syncs).
+ * Each scene keeps its own grid, sound speed, dt and time; scenes never
+ * interact. */
+int sph_set_scenes(sph_ctx* ctx, uint32_t n_scenes, const sph_scene* scenes);
+
+/* Upload n particles from HOST arrays (copied):
+ *   pos   n*3 FP64 absolute positions (converted on the device to a cell index
+ *         plus an FP32 offset from the cell centre, paper Section 2.3),
+ *   vel   n*3 FP32 (ignored, i.e. zero, for boundary particles),
+ *   delta n   FP32 relative density rho/rho0 - 1,
+ *   mass  n   FP32 (> 0),
+ *   type  n   SPH_FLUID / SPH_BOUNDARY,
+ *   scene n   scene index, or NULL for all-zero.
+ * Particle i keeps id i for sph_download.  Sorts the particles and resets
+ * step count, time and dt (the first sph_step computes dt0 from one forces
+ * call).  Errors: SPH_ERR_CAPACITY (n > max_particles), SPH_ERR_ARG (bad
+ * type/scene/mass), SPH_ERR_OUT_OF_DOMAIN (a position outside its scene's
+ * domain on a non-periodic axis), SPH_ERR_NONFINITE.  Synchronises `stream`. */
+int sph_upload(sph_ctx* ctx, uint32_t n, const double* pos, const float* vel, const float* delta,
+               const float* mass, const uint8_t* type, const uint32_t* scene, void* stream);
+
+/* Same as sph_upload with DEVICE arrays of the same layouts. */
+int sph_upload_device(sph_ctx* ctx, uint32_t n, const double* pos_dev, const float* vel_dev,
+                      const float* delta_dev, const float* mass_dev, const uint8_t* type_dev,
+                      const uint32_t* scene_dev, void* stream);
+
+/* Neighbour pipeline on the current state: cell hash, key sort by (cell,
+ * type, id), reorder, cell start/end, split neighbour list (paper
+ * Sections 2.3 and 4: fixed-size, neighbour-major, fluid neighbours from the
+ * front and boundary neighbours from the back, end-of-list markers). */
+int sph_build_neighbors(sph_ctx* ctx, void* stream);
+
+/* Particle interactions on the current state with the current neighbour
+ * list (paper Section 2.1): acceleration and density rate of every
+ * particle into the library's force buffer (read with sph_download_forces). */
+int sph_forces(sph_ctx* ctx, void* stream);
+
+/* nsteps predictor-corrector steps, each: neighbour pipeline, forces at n,
+ * predictor (dt/2), forces at the predicted state, corrector (dt), CFL dt
+ * for the next step.  Replays a captured CUDA graph per step. */
+int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
+
+/* Same work as sph_step, launched kernel by kernel (no graph) with CUDA
+ * events recorded on `stream` between the launches; adds the elapsed
+ * milliseconds of each phase to phase_ms[0..7]: 0 dt, 1 hash, 2 scan,
+ * 3 scatter, 4 in-cell sort + reorder, 5 neighbour-list build,
+ * 6 forces + predictor, 7 forces + corrector.  Synchronises after each
+ * step (measurement aid; sph_step is the production path). */
+int sph_step_profiled(sph_ctx* ctx, uint32_t nsteps, void* stream, double* phase_ms);
+
+/* Download the state in upload order into HOST arrays (any may be NULL):
+ * pos n*3 FP64, vel n*3 FP32, delta n FP32.  Particles removed from the
+ * domain read as NaN.  n must equal the uploaded count.  Synchronises. */
+int sph_download(sph_ctx* ctx, uint32_t n, double* pos, float* vel, float* delta, void* stream);
+
+/* Same as sph_download into DEVICE arrays (no host synchronisation). */
+int sph_download_device(sph_ctx* ctx, uint32_t n, double* pos_dev, float* vel_dev,
+                        float* delta_dev, void* stream);
+
+/* Download the last sph_forces result in upload order: acc n*3, drho n
+ * (FP32, density rate d rho/dt).  HOST arrays; synchronises. */
+int sph_download_forces(sph_ctx* ctx, uint32_t n, float* acc, float* drho, void* stream);
+
+/* Download the neighbour lists in upload order (for checking): counts
+ * n*2 (fluid, boundary neighbours written), ids n*max_neibs upload ids of
+ * the neighbours, fluid first then boundary, unused slots 0xFFFFFFFF.
+ * HOST arrays; synchronises. */
+int sph_download_neighbors(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream);
+
+/* Read device counters into *out (synchronises `stream`).  Returns the
+ * sticky device error as a code (SPH_ERR_NEIB_OVERFLOW, SPH_ERR_NONFINITE,
+ * SPH_ERR_TIMEOUT) if one is set, else SPH_OK; *out is filled either way. */
+int sph_get_stats(sph_ctx* ctx, sph_stats* out, void* stream);
+
+/* Per-scene dt and simulated time (n_scenes entries each, HOST, nullable). */
+int sph_get_scene_times(sph_ctx* ctx, double* dt, double* time, void* stream);
+
+/* Clear the sticky device error word. */
+int sph_clear_error(sph_ctx* ctx, void* stream);
+
+/* Wait for the stream and return the sticky device error (as sph_get_stats). */
+int sph_sync(sph_ctx* ctx, void* stream);
+
+/* Human-readable text of a return code (static storage). */
+const char* sph_strerror(int code);
+
+/* Free every buffer of the context (synchronises the device). */
+void sph_destroy(sph_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPH_GB300_H */

@@ -73,10 +73,10 @@ def _load():
             lib.ora_neighbors.restype = ctypes.c_int64
             lib.ora_neighbors.argtypes = [P, ctypes.c_int, dp_, ctypes.c_int, ctypes.c_int64, i64p, i32p]
             lib.ora_rhs.restype = ctypes.c_int
-            lib.ora_rhs.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, dp_, dp_]
+            lib.ora_rhs.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, dp_, dp_, dp_]
             lib.ora_rhs_sample.restype = ctypes.c_int
             lib.ora_rhs_sample.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int,
-                                           i32p, dp_, dp_, i32p]
+                                           i32p, dp_, dp_, i32p, dp_]
             lib.ora_cfl_dt.restype = ctypes.c_double
             lib.ora_cfl_dt.argtypes = [P, ctypes.c_int, dp_, u8p]
             lib.ora_step.restype = ctypes.c_int
@@ -149,37 +149,41 @@ def neighbors(p: Params, pos, brute=False):
         cap = -tot
 
 
-def rhs(p: Params, pos, vel, delta, mass, ptype):
-    """(a[n,3], drho[n]) at the given state (FP64)."""
+def rhs(p: Params, pos, vel, delta, mass, ptype, with_mag=False):
+    """(a[n,3], drho[n]) at the given state (FP64); with_mag adds mag[n,2],
+    the summed magnitudes of the momentum and continuity pair terms."""
     lib = _load()
     pos, pp = _d(pos); vel, vp = _d(vel); delta, dp_ = _d(delta); mass, mp = _d(mass)
     ptype, tp = _u8(ptype)
     n = pos.shape[0]
     a = np.zeros((n, 3)); drho = np.zeros(n)
+    mag = np.zeros((n, 2)) if with_mag else None
     rc = lib.ora_rhs(ctypes.byref(p), n, pp, vp, dp_, mp, tp,
                      a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                     drho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+                     drho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                     None if mag is None else mag.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise RuntimeError("ora_rhs failed")
-    return a, drho
+    return (a, drho, mag) if with_mag else (a, drho)
 
 
 def rhs_sample(p: Params, pos, vel, delta, mass, ptype, sample):
-    """(a[s,3], drho[s], n_neighbours[s]) for particles `sample` only."""
+    """(a[s,3], drho[s], n_neighbours[s], mag[s,2]) for particles `sample` only."""
     lib = _load()
     pos, pp = _d(pos); vel, vp = _d(vel); delta, dp_ = _d(delta); mass, mp = _d(mass)
     ptype, tp = _u8(ptype)
     sample = np.ascontiguousarray(sample, np.int32)
     ns = sample.shape[0]
-    a = np.zeros((ns, 3)); drho = np.zeros(ns); nnb = np.zeros(ns, np.int32)
+    a = np.zeros((ns, 3)); drho = np.zeros(ns); nnb = np.zeros(ns, np.int32); mag = np.zeros((ns, 2))
     rc = lib.ora_rhs_sample(ctypes.byref(p), pos.shape[0], pp, vp, dp_, mp, tp, ns,
                             sample.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                             a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                             drho.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                            nnb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+                            nnb.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                            mag.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     if rc != 0:
         raise RuntimeError("ora_rhs_sample failed")
-    return a, drho, nnb
+    return a, drho, nnb, mag
 
 
 def cfl_dt(p: Params, a, ptype):

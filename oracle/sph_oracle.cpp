@@ -266,10 +266,14 @@ struct State {
     std::vector<T> x, u, delta;  /* 3n, 3n, n */
 };
 
+/* mag (nullable): receives the summed magnitudes of the pair terms,
+ * mag[0] = |g| + sum_j |momentum term_ij|, mag[1] = sum_j |continuity term_ij|
+ * (the scale of the cancellation in each sum; used to state FP32 error bounds). */
 template <class T>
 void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* delta,
                   const double* m, const uint8_t* type, T alpha, const T* rho, const T* phat,
-                  const int32_t* nb, int64_t nnb, T* a_out, T* drho_out) {
+                  const int32_t* nb, int64_t nnb, T* a_out, T* drho_out, double* mag = nullptr) {
+    double mag_a = 0.0, mag_d = 0.0;
     const double h = P.h;
     const bool fluid_i = type[i] == 0;
     T ui[3];
@@ -288,6 +292,7 @@ void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* d
         for (int c = 0; c < 3; ++c) uij[c] = ui[c] - (fluid_j ? u[3 * j + c] : T(0.0));
         T udotx = uij[0] * d[0] + uij[1] * d[1] + uij[2] * d[2];
         drho += T(m[j]) * udotx * F;
+        if (mag) mag_d += std::fabs(pv(T(m[j]) * udotx * F));
         if (!fluid_i) continue;
         T bracket = phat[i] + phat[j];
         if (P.visc_model == 0 && pv(udotx) < 0.0) {
@@ -297,10 +302,16 @@ void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* d
         }
         T coef = T(m[j]) * bracket * F;
         for (int c = 0; c < 3; ++c) a[c] -= coef * d[c];
+        if (mag) mag_a += std::fabs(pv(coef)) * std::sqrt(pv(r2));
         if (P.visc_model == 1) {
             T lam = T(4.0 * P.nu * m[j]) * F / (rho[i] + rho[j]);
             for (int c = 0; c < 3; ++c) a[c] += lam * uij[c];
+            if (mag) mag_a += std::fabs(pv(lam)) * std::sqrt(pv(uij[0] * uij[0] + uij[1] * uij[1] + uij[2] * uij[2]));
         }
+    }
+    if (mag) {
+        mag[0] = mag_a + (fluid_i ? std::sqrt(P.g[0] * P.g[0] + P.g[1] * P.g[1] + P.g[2] * P.g[2]) : 0.0);
+        mag[1] = mag_d;
     }
     if (fluid_i) {
         for (int c = 0; c < 3; ++c) a_out[c] = a[c] + T(P.g[c]);
@@ -432,13 +443,25 @@ int64_t ora_neighbors(const ora_params* P, int n, const double* x, int brute, in
     return tot;
 }
 
-/* Time derivatives of all particles at the given state.  a: n*3, drho: n. */
+/* Time derivatives of all particles at the given state.  a: n*3, drho: n,
+ * mag: n*2 summed term magnitudes (nullable, see particle_rhs). */
 int ora_rhs(const ora_params* P, int n, const double* x, const double* u, const double* delta,
-            const double* m, const uint8_t* type, double* a, double* drho) {
+            const double* m, const uint8_t* type, double* a, double* drho, double* mag) {
     if (!P || n < 0) return -1;
     Nbrs N;
     neighbors_grid(*P, n, x, N);
     rhs_all<double>(*P, n, x, u, delta, m, type, P->alpha, N, a, drho);
+    if (mag) {
+        std::vector<double> rho(n), phat(n), at(3);
+        for (int i = 0; i < n; ++i) {
+            rho[i] = P->rho0 * (1.0 + delta[i]);
+            phat[i] = eos_pressure<double>(delta[i], *P) / (rho[i] * rho[i]);
+        }
+        double dr;
+        for (int i = 0; i < n; ++i)
+            particle_rhs<double>(*P, i, x, u, delta, m, type, P->alpha, rho.data(), phat.data(),
+                                 N.idx.data() + N.off[i], N.off[i + 1] - N.off[i], at.data(), &dr, mag + 2 * i);
+    }
     return 0;
 }
 
@@ -446,7 +469,7 @@ int ora_rhs(const ora_params* P, int n, const double* x, const double* u, const 
  * with neighbours searched among all n particles. */
 int ora_rhs_sample(const ora_params* P, int n, const double* x, const double* u,
                    const double* delta, const double* m, const uint8_t* type, int ns,
-                   const int32_t* sidx, double* a, double* drho, int32_t* nnb) {
+                   const int32_t* sidx, double* a, double* drho, int32_t* nnb, double* mag) {
     if (!P || n < 0 || ns < 0) return -1;
     Bins B;
     std::vector<int32_t> nb;
@@ -473,7 +496,7 @@ int ora_rhs_sample(const ora_params* P, int n, const double* x, const double* u,
         }
         if (nnb) nnb[s] = (int32_t)nb.size();
         particle_rhs<double>(*P, i, x, u, delta, m, type, P->alpha, rho.data(), phat.data(),
-                             nb.data(), (int64_t)nb.size(), a + 3 * s, drho + s);
+                             nb.data(), (int64_t)nb.size(), a + 3 * s, drho + s, mag ? mag + 2 * s : nullptr);
     }
     return 0;
 }

@@ -1,0 +1,285 @@
+"""GB300-native weakly-compressible SPH hot path (arXiv 2207.11328).
+
+Thin Python binding of the C ABI declared in include/sph.h: argument
+marshalling only.  Every step of the path runs in the CUDA library
+(libsph_gb300.so, built for sm_103a by ``paper_2207_11328_gb300._build``);
+there is no CPU fallback: importing the binding without the library raises.
+
+    from paper_2207_11328_gb300 import Simulation, scenes
+    sim = Simulation.from_scene(scenes.periodic_box())
+    sim.step(100)
+    pos, vel, delta = sim.download()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import scenes  # noqa: F401  (seeded generators; no method arithmetic)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
+
+SPH_OK = 0
+_ERRNAMES = {-1: "SPH_ERR_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_CAPACITY", -4: "SPH_ERR_NEIB_OVERFLOW",
+             -5: "SPH_ERR_OUT_OF_DOMAIN", -6: "SPH_ERR_NONFINITE", -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE"}
+
+
+class SphError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {_ERRNAMES.get(code, code)} ({_lib().sph_strerror(code).decode()})")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("dp", ctypes.c_double), ("h", ctypes.c_double), ("kernel_radius", ctypes.c_double),
+                ("rho0", ctypes.c_double), ("c0", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("visc_model", ctypes.c_int32), ("pad0", ctypes.c_int32),
+                ("alpha", ctypes.c_double), ("nu", ctypes.c_double), ("g", ctypes.c_double * 3),
+                ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
+                ("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3),
+                ("periodic_mask", ctypes.c_uint32), ("max_particles", ctypes.c_uint32),
+                ("max_neibs", ctypes.c_uint32), ("n_scenes", ctypes.c_uint32)]
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3),
+                ("periodic_mask", ctypes.c_uint32), ("pad0", ctypes.c_uint32), ("c0", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_active", ctypes.c_uint32), ("n_removed", ctypes.c_uint32),
+                ("max_neibs_seen", ctypes.c_uint32), ("error_bits", ctypes.c_uint32),
+                ("steps", ctypes.c_uint64), ("dt", ctypes.c_double), ("time", ctypes.c_double),
+                ("n_cells", ctypes.c_uint32), ("kernels_per_step", ctypes.c_uint32),
+                ("list_entries", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
+
+
+_LIB = None
+
+# exported entry points and their signatures (argument marshalling only)
+_vp = ctypes.c_void_p
+_SIGS = {
+    "sph_create": [ctypes.POINTER(Params), ctypes.POINTER(_vp)],
+    "sph_set_scenes": [_vp, ctypes.c_uint32, ctypes.POINTER(SceneDesc)],
+    "sph_upload": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sph_upload_device": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sph_build_neighbors": [_vp, _vp],
+    "sph_forces": [_vp, _vp],
+    "sph_step": [_vp, ctypes.c_uint32, _vp],
+    "sph_step_profiled": [_vp, ctypes.c_uint32, _vp, _vp],
+    "sph_download": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
+    "sph_download_device": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
+    "sph_download_forces": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
+    "sph_download_neighbors": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
+    "sph_get_stats": [_vp, ctypes.POINTER(Stats), _vp],
+    "sph_get_scene_times": [_vp, _vp, _vp, _vp],
+    "sph_clear_error": [_vp, _vp],
+    "sph_sync": [_vp, _vp],
+    "sph_strerror": [ctypes.c_int],
+    "sph_destroy": [_vp],
+}
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                              "(run python -m paper_2207_11328_gb300._build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        lib.sph_strerror.restype = ctypes.c_char_p
+        lib.sph_destroy.restype = None
+        _LIB = lib
+    return _LIB
+
+
+def _check(rc, where):
+    if rc != SPH_OK:
+        raise SphError(rc, where)
+
+
+def _ptr(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream):
+    """cudaStream_t of a torch stream (or None for the legacy default stream)."""
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def params_from_scene(scene, max_particles=None, max_neibs=128):
+    p = Params()
+    p.dp, p.h, p.kernel_radius = scene.dp, scene.h, scene.kernel_radius
+    p.rho0, p.c0, p.gamma = scene.rho0, scene.c0, float(scene.gamma)
+    p.visc_model, p.alpha, p.nu = scene.visc, scene.alpha, scene.nu
+    p.g[:] = list(scene.g)
+    p.cfl, p.dt_fixed = scene.cfl, scene.dt_fixed
+    p.origin[:] = list(scene.origin)
+    p.size[:] = list(scene.size)
+    p.periodic_mask = scene.periodic
+    p.max_particles = int(max_particles or max(scene.n, 1))
+    p.max_neibs = int(max_neibs)
+    p.n_scenes = 1
+    return p
+
+
+class Simulation:
+    """One library context (sph_ctx) on the current CUDA device."""
+
+    def __init__(self, params: Params, scenes_desc=None):
+        lib = _lib()
+        h = ctypes.c_void_p()
+        _check(lib.sph_create(ctypes.byref(params), ctypes.byref(h)), "sph_create")
+        self._h = h
+        self.params = params
+        self.n = 0
+        if scenes_desc:
+            arr = (SceneDesc * len(scenes_desc))()
+            for k, d in enumerate(scenes_desc):
+                arr[k].origin[:] = list(d["origin"])
+                arr[k].size[:] = list(d["size"])
+                arr[k].periodic_mask = int(d.get("periodic", 0))
+                arr[k].c0 = float(d["c0"])
+            _check(lib.sph_set_scenes(self._h, len(scenes_desc), arr), "sph_set_scenes")
+        self.n_scenes = len(scenes_desc) if scenes_desc else 1
+
+    @classmethod
+    def from_scene(cls, scene, max_particles=None, max_neibs=128, upload=True, stream=None):
+        sim = cls(params_from_scene(scene, max_particles, max_neibs), scene.scenes)
+        if upload:
+            sim.upload(scene, stream=stream)
+        return sim
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib().sph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- upload / download -------------------------------------------------
+    def upload(self, scene=None, *, pos=None, vel=None, delta=None, mass=None, ptype=None, scene_id=None,
+               stream=None):
+        if scene is not None:
+            pos, vel, delta, mass, ptype = scene.pos, scene.vel, scene.delta, scene.mass, scene.ptype
+            scene_id = scene.scene if scene.scenes else None
+        pos = np.ascontiguousarray(pos, np.float64)
+        vel = np.ascontiguousarray(vel, np.float32)
+        delta = np.ascontiguousarray(delta, np.float32)
+        mass = np.ascontiguousarray(mass, np.float32)
+        ptype = np.ascontiguousarray(ptype, np.uint8)
+        sid = None if scene_id is None else np.ascontiguousarray(scene_id, np.uint32)
+        n = pos.shape[0]
+        _check(_lib().sph_upload(self._h, n, _ptr(pos), _ptr(vel), _ptr(delta), _ptr(mass), _ptr(ptype),
+                                 _ptr(sid), _stream_handle(stream)), "sph_upload")
+        self.n = n
+
+    def upload_device(self, pos, vel, delta, mass, ptype, scene_id=None, stream=None):
+        """Upload from torch CUDA tensors (float64 pos, float32 vel/delta/mass, uint8 type)."""
+        n = int(pos.shape[0])
+        sid = None if scene_id is None else ctypes.c_void_p(scene_id.data_ptr())
+        _check(_lib().sph_upload_device(self._h, n, ctypes.c_void_p(pos.data_ptr()), ctypes.c_void_p(vel.data_ptr()),
+                                        ctypes.c_void_p(delta.data_ptr()), ctypes.c_void_p(mass.data_ptr()),
+                                        ctypes.c_void_p(ptype.data_ptr()), sid, _stream_handle(stream)),
+               "sph_upload_device")
+        self.n = n
+
+    def download(self, stream=None, out=None):
+        """(pos, vel, delta) in upload order; `out` = preallocated (pos, vel, delta) host arrays."""
+        n = self.n
+        if out is None:
+            pos = np.empty((n, 3), np.float64)
+            vel = np.empty((n, 3), np.float32)
+            delta = np.empty(n, np.float32)
+        else:
+            pos, vel, delta = out
+            assert pos.dtype == np.float64 and vel.dtype == np.float32 and delta.dtype == np.float32
+            assert pos.flags.c_contiguous and vel.flags.c_contiguous and delta.flags.c_contiguous
+        _check(_lib().sph_download(self._h, n, _ptr(pos), _ptr(vel), _ptr(delta), _stream_handle(stream)),
+               "sph_download")
+        return pos, vel, delta
+
+    def download_device(self, pos, vel, delta, stream=None):
+        """Download into torch CUDA tensors (no host synchronisation)."""
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        _check(_lib().sph_download_device(self._h, self.n, p(pos), p(vel), p(delta), _stream_handle(stream)),
+               "sph_download_device")
+
+    def download_forces(self, stream=None):
+        n = self.n
+        acc = np.empty((n, 3), np.float32)
+        drho = np.empty(n, np.float32)
+        _check(_lib().sph_download_forces(self._h, n, _ptr(acc), _ptr(drho), _stream_handle(stream)),
+               "sph_download_forces")
+        return acc, drho
+
+    def download_neighbors(self, stream=None):
+        n = self.n
+        mn = self.params.max_neibs
+        counts = np.empty((n, 2), np.uint32)
+        ids = np.empty((n, mn), np.uint32)
+        _check(_lib().sph_download_neighbors(self._h, n, _ptr(counts), _ptr(ids), _stream_handle(stream)),
+               "sph_download_neighbors")
+        return counts, ids
+
+    # ---- the hot path ------------------------------------------------------
+    def build_neighbors(self, stream=None):
+        _check(_lib().sph_build_neighbors(self._h, _stream_handle(stream)), "sph_build_neighbors")
+
+    def forces(self, stream=None):
+        _check(_lib().sph_forces(self._h, _stream_handle(stream)), "sph_forces")
+
+    def step(self, nsteps=1, stream=None):
+        _check(_lib().sph_step(self._h, int(nsteps), _stream_handle(stream)), "sph_step")
+
+    PHASES = ("dt", "hash", "scan", "scatter", "reorder", "build", "forces_predict", "forces_correct")
+
+    def step_profiled(self, nsteps=1, stream=None):
+        """Steps launched kernel by kernel with CUDA events between them;
+        returns {phase: total ms}."""
+        ms = np.zeros(8, np.float64)
+        _check(_lib().sph_step_profiled(self._h, int(nsteps), _stream_handle(stream), _ptr(ms)),
+               "sph_step_profiled")
+        return dict(zip(self.PHASES, ms.tolist()))
+
+    # ---- counters ----------------------------------------------------------
+    def stats(self, stream=None, check=True):
+        s = Stats()
+        rc = _lib().sph_get_stats(self._h, ctypes.byref(s), _stream_handle(stream))
+        if check:
+            _check(rc, "sph_get_stats")
+        return s.as_dict() | {"rc": rc}
+
+    def scene_times(self, stream=None):
+        dt = np.empty(self.n_scenes, np.float64)
+        t = np.empty(self.n_scenes, np.float64)
+        _check(_lib().sph_get_scene_times(self._h, _ptr(dt), _ptr(t), _stream_handle(stream)), "sph_get_scene_times")
+        return dt, t
+
+    def clear_error(self, stream=None):
+        _check(_lib().sph_clear_error(self._h, _stream_handle(stream)), "sph_clear_error")
+
+    def sync(self, stream=None):
+        _check(_lib().sph_sync(self._h, _stream_handle(stream)), "sph_sync")

@@ -1,0 +1,246 @@
+// Particle interactions and time integration (paper Section 2.1; readings
+// of the passages the paper leaves to its references are stated inline).
+//
+//   drho_i/dt = sum_j m_j (u_i - u_j).x_ij F_ij                        (C1)
+//   du_i/dt   = -sum_j m_j (P_i/rho_i^2 + P_j/rho_j^2 + Pi_ij) x_ij F_ij  (C2)
+//               + sum_j 4 nu m_j/(rho_i + rho_j) F_ij (u_i - u_j) + g     (C3)
+//   Pi_ij = -alpha h c0 mu_ij / rhobar_ij for u_ij.x_ij < 0,
+//   mu_ij = u_ij.x_ij/(r^2 + 0.01 h^2), rhobar = (rho_i + rho_j)/2          (C4)
+//   F = (1/r) dW/dr = aF (q - 2)^3 for q = r/h < 2 (Wendland C2, Section 4)
+//   Dynamic boundary particles: zero velocity, continuity only      (C5)
+//
+// One thread per particle, sorted order.  The neighbour list is read
+// neighbour-major (a warp reads 128 contiguous bytes per slot), fluid slots
+// from the front and boundary slots from the back (split list, Section 4),
+// each with its own loop.  Per neighbour the kernel gathers pos4 + vel4 +
+// P/rho^2 (36 bytes, served by L1/L2: neighbours of consecutive particles
+// are the same cell-sorted particles).  P/rho^2 is computed once per
+// particle by whichever kernel writes delta, not once per pair.
+// The predictor (dt/2) and corrector (dt) updates of reading C6 are fused
+// into the epilogues of the two force passes; the corrector pass reduces
+// max |a|^2 per scene (warp reduction + one atomic) for the CFL dt (C7).
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+namespace {
+
+constexpr int kBlock = 128;
+
+__device__ __forceinline__ float cell_delta(uint32_t bits2, float cell) {
+    // bits2 = d + 1 in {0, 1, 2}  ->  d * cell
+    return bits2 == 0u ? -cell : (bits2 == 2u ? cell : 0.0f);
+}
+
+struct Acc {
+    float ax, ay, az, drho;
+};
+
+// One neighbour of a fluid particle.  BND: the neighbour is a boundary
+// particle (mass stored negated, velocity zero).
+template <int VISC, bool BND>
+__device__ __forceinline__ void fluid_pair(uint32_t e, const float4& pi, const float4& vi, float phat_i,
+                                           const float4* __restrict__ pos, const float4* __restrict__ vel,
+                                           const float* __restrict__ phat, float cx, float cy, float cz,
+                                           float pi_coef, const Phys& ph, Acc& acc) {
+    const uint32_t j = e >> kCodeBits;
+    const float4 pj = pos[j];
+    const float4 vj = vel[j];
+    const float phat_j = phat[j];
+    const float rx = pi.x - pj.x - cell_delta(e & 3u, cx);
+    const float ry = pi.y - pj.y - cell_delta((e >> 2) & 3u, cy);
+    const float rz = pi.z - pj.z - cell_delta((e >> 4) & 3u, cz);
+    const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
+    const float r = r2 * rsqrtf(r2);
+    const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
+    const float mj = BND ? -pj.w : pj.w;
+    const float mF = mj * ph.aF * (t * t * t);
+    const float ux = BND ? vi.x : vi.x - vj.x;
+    const float uy = BND ? vi.y : vi.y - vj.y;
+    const float uz = BND ? vi.z : vi.z - vj.z;
+    const float udx = fmaf(ux, rx, fmaf(uy, ry, uz * rz));
+    acc.drho = fmaf(mF, udx, acc.drho);
+    float bracket = phat_i + phat_j;
+    if (VISC == SPH_VISC_ARTIFICIAL) {
+        if (udx < 0.f) {
+            const float den = (r2 + ph.eps_h2) * fmaf(0.5f, vi.w + vj.w, 1.0f);
+            bracket -= pi_coef * __fdividef(udx, den);
+        }
+    }
+    const float coef = mF * bracket;
+    acc.ax = fmaf(-coef, rx, acc.ax);
+    acc.ay = fmaf(-coef, ry, acc.ay);
+    acc.az = fmaf(-coef, rz, acc.az);
+    if (VISC == SPH_VISC_LAMINAR) {
+        const float lam = ph.nu4 * ph.inv_rho0 * __fdividef(mF, 2.0f + vi.w + vj.w);
+        acc.ax = fmaf(lam, ux, acc.ax);
+        acc.ay = fmaf(lam, uy, acc.ay);
+        acc.az = fmaf(lam, uz, acc.az);
+    }
+}
+
+template <int VISC, int MODE>
+__global__ void __launch_bounds__(kBlock) k_forces(
+    const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
+    float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
+    const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
+    const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
+    int acc_dt) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t s = pinfo[i];
+        const SceneDev& sc = scenes[s];
+        const float4 pi = pos[i];
+        const float4 vi = vel[i];
+        const uint32_t cnt = ncount[i];
+        const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        const bool fluid_i = pi.w > 0.f;
+        const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
+        Acc acc{0.f, 0.f, 0.f, 0.f};
+        if (fluid_i) {
+            const float phat_i = phat[i];
+            const float pic = sc.pi_coef;
+            const uint32_t* lp = nlist + i;
+#pragma unroll 2
+            for (uint32_t k = 0; k < nf; ++k, lp += ph.stride)
+                fluid_pair<VISC, false>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+            lp = nlist + (size_t)(ph.max_neibs - 1) * ph.stride + i;
+            for (uint32_t k = 0; k < nb; ++k, lp -= ph.stride)
+                fluid_pair<VISC, true>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+            acc.ax += ph.g[0];
+            acc.ay += ph.g[1];
+            acc.az += ph.g[2];
+        } else {
+            // boundary particle: continuity over its fluid neighbours, u_i = 0
+            const uint32_t* lp = nlist + i;
+#pragma unroll 2
+            for (uint32_t k = 0; k < nf; ++k, lp += ph.stride) {
+                const uint32_t e = __ldg(lp);
+                const uint32_t j = e >> kCodeBits;
+                const float4 pj = pos[j];
+                const float4 vj = vel[j];
+                const float rx = pi.x - pj.x - cell_delta(e & 3u, cx);
+                const float ry = pi.y - pj.y - cell_delta((e >> 2) & 3u, cy);
+                const float rz = pi.z - pj.z - cell_delta((e >> 4) & 3u, cz);
+                const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
+                const float r = r2 * rsqrtf(r2);
+                const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
+                const float mF = pj.w * ph.aF * (t * t * t);
+                const float udx = -fmaf(vj.x, rx, fmaf(vj.y, ry, vj.z * rz));
+                acc.drho = fmaf(mF, udx, acc.drho);
+            }
+        }
+
+        if (MODE == kForcesOnly) {
+            force_out[i] = make_float4(acc.ax, acc.ay, acc.az, acc.drho);
+        } else {
+            const float dt = dyn[s].dt;
+            if (MODE == kPredict) {
+                const float hd = 0.5f * dt;
+                float4 po = pi, vo = vi;
+                vo.w = fmaf(hd * ph.inv_rho0, acc.drho, vi.w);
+                if (fluid_i) {
+                    vo.x = fmaf(hd, acc.ax, vi.x);
+                    vo.y = fmaf(hd, acc.ay, vi.y);
+                    vo.z = fmaf(hd, acc.az, vi.z);
+                    po.x = fmaf(hd, vi.x, pi.x);
+                    po.y = fmaf(hd, vi.y, pi.y);
+                    po.z = fmaf(hd, vi.z, pi.z);
+                }
+                io_pos[i] = po;
+                io_vel[i] = vo;
+                io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
+            } else {  // kCorrect: state n in io_*, overwritten by n+1
+                float4 po = io_pos[i], vo = io_vel[i];
+                const float un_x = vo.x, un_y = vo.y, un_z = vo.z;
+                vo.w = fmaf(dt * ph.inv_rho0, acc.drho, vo.w);
+                if (fluid_i) {
+                    vo.x = fmaf(dt, acc.ax, un_x);
+                    vo.y = fmaf(dt, acc.ay, un_y);
+                    vo.z = fmaf(dt, acc.az, un_z);
+                    const float hd = 0.5f * dt;
+                    po.x = fmaf(hd, un_x + vo.x, po.x);
+                    po.y = fmaf(hd, un_y + vo.y, po.y);
+                    po.z = fmaf(hd, un_z + vo.z, po.z);
+                }
+                io_pos[i] = po;
+                io_vel[i] = vo;
+                io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
+                const float chk = po.x + po.y + po.z + vo.x + vo.y + vo.z + vo.w;
+                if (!isfinite(chk)) atomicOr(&st->error_bits, SPH_EBIT_NONFINITE);
+            }
+        }
+        if (MODE == kCorrect || acc_dt) {
+            const float a2 = fluid_i ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
+            const uint32_t bits = __float_as_uint(a2);
+            const unsigned mask = __activemask();
+            const unsigned same = __match_any_sync(mask, s);
+            if (same == mask) {
+                const uint32_t m = __reduce_max_sync(mask, bits);
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1) && m) atomicMax(&dyn[s].amax2_bits, m);
+            } else if (bits) {
+                atomicMax(&dyn[s].amax2_bits, bits);
+            }
+        }
+    }
+}
+
+// One thread per scene: dt for the coming step (reading C7), simulated
+// time, reset of the |a|^2 accumulator.
+__global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
+                     uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance) {
+    for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
+        double dt;
+        if (dt_fixed > 0.0) {
+            dt = dt_fixed;
+        } else {
+            dt = scenes[s].dt_cap;
+            const double a2 = (double)__uint_as_float(dyn[s].amax2_bits);
+            if (a2 > 0.0) dt = fmin(dt, cfl * sqrt(h / sqrt(a2)));
+        }
+        dyn[s].dt = (float)dt;
+        dyn[s].dt_d = dt;
+        if (advance) dyn[s].time += dt;
+        dyn[s].amax2_bits = 0u;
+    }
+    if (threadIdx.x == 0 && advance) st->steps += 1ull;
+}
+
+template <int VISC>
+void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
+                     cudaStream_t st) {
+    const unsigned grid = g.cap ? (g.cap + kBlock - 1) / kBlock : 1;
+    switch (mode) {
+        case kForcesOnly:
+            k_forces<VISC, kForcesOnly><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr,
+                                                                  nullptr, b.force, b.pinfo[cur], b.nlist, b.ncount,
+                                                                  b.scenes, b.dyn, b.status, ph, acc_dt);
+            break;
+        case kPredict:
+            k_forces<VISC, kPredict><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s,
+                                                               b.phat_s, nullptr, b.pinfo[cur], b.nlist, b.ncount,
+                                                               b.scenes, b.dyn, b.status, ph, 0);
+            break;
+        case kCorrect:
+            k_forces<VISC, kCorrect><<<grid, kBlock, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur],
+                                                               b.phat[cur], nullptr, b.pinfo[cur], b.nlist, b.ncount,
+                                                               b.scenes, b.dyn, b.status, ph, 0);
+            break;
+    }
+}
+
+}  // namespace
+
+void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
+                   cudaStream_t st) {
+    if (ph.visc == SPH_VISC_LAMINAR)
+        launch_forces_v<SPH_VISC_LAMINAR>(b, cur, g, ph, mode, acc_dt, st);
+    else
+        launch_forces_v<SPH_VISC_ARTIFICIAL>(b, cur, g, ph, mode, acc_dt, st);
+}
+
+void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st) {
+    k_dt<<<1, 256, 0, st>>>(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, advance_time);
+}
+
+}  // namespace sphg

@@ -1,0 +1,389 @@
+// Neighbour pipeline (paper Section 2.3 and Section 4):
+//   cell hash -> counting sort by cell (histogram, exclusive scan, scatter)
+//   -> in-cell order by (type, id) + reorder of the particle arrays
+//   -> cell start/end table (the scan itself) -> split neighbour list.
+//
+// Deterministic: the histogram counts are order-free, the in-cell rank is a
+// comparison count on the unique key (type, id), so the sorted arrays are
+// bit-identical from run to run whatever order the atomics took.
+#include "sph_internal.cuh"
+
+namespace sphg {
+
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;                       // per thread
+constexpr int kScanTile = kScanThreads * kScanItems;  // buckets per block
+
+// ---------------------------------------------------------------------
+// a1: cell hash.  New cell = old cell + floor(offset/cell + 1/2) per axis
+// (cell-relative positions never leave FP32 range); periodic axes wrap;
+// on other axes a particle outside the grid goes to the sentinel bucket
+// (removed during the sort, paper "The GPU in GPUSPH").
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_hash(const float4* __restrict__ pos, const uint32_t* __restrict__ cell,
+                                                 const uint32_t* __restrict__ pinfo,
+                                                 const SceneDev* __restrict__ scenes,
+                                                 const DevStatus* __restrict__ st, uint32_t* __restrict__ key,
+                                                 uint32_t* __restrict__ slot, uint32_t* __restrict__ count,
+                                                 uint32_t sentinel) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SceneDev& sc = scenes[pinfo[i]];
+        const float4 p = pos[i];
+        const uint32_t c = cell[i];
+        const int sx = cell_shift(p.x, sc.inv_cell_f[0]);
+        const int sy = cell_shift(p.y, sc.inv_cell_f[1]);
+        const int sz = cell_shift(p.z, sc.inv_cell_f[2]);
+        uint32_t k = c;
+        if ((sx | sy | sz) != 0) {
+            int cx, cy, cz;
+            decode_local(c - sc.cell_offset, sc, cx, cy, cz);
+            int nc[3] = {cx + sx, cy + sy, cz + sz};
+            bool out = false;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int n_a = sc.ncell[a];
+                if ((sc.periodic >> a) & 1u) {
+                    nc[a] %= n_a;
+                    if (nc[a] < 0) nc[a] += n_a;
+                } else if (nc[a] < 0 || nc[a] >= n_a) {
+                    out = true;
+                }
+            }
+            k = out ? sentinel
+                    : sc.cell_offset + (uint32_t)nc[0] +
+                          (uint32_t)sc.ncell[0] * ((uint32_t)nc[1] + (uint32_t)sc.ncell[1] * (uint32_t)nc[2]);
+        }
+        key[i] = k;
+        slot[i] = atomicAdd(&count[k], 1u);
+    }
+}
+
+// ---------------------------------------------------------------------
+// a2/a4: exclusive scan of the bucket counts -> cell start table.
+// Three passes: block sums, scan of block sums, down-sweep.  The down-sweep
+// zeroes the counts for the next hash and publishes the in-domain count.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t wtotal;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        const int nw = blockDim.x >> 5;
+        const uint32_t s = lane < nw ? wsum[lane] : 0u;
+        const uint32_t si = warp_incl_scan(s);
+        if (lane < nw) wsum[lane] = si - s;
+        if (lane == nw - 1) wtotal = si;
+    }
+    __syncthreads();
+    const uint32_t res = wsum[w] + inc - v;
+    *total = wtotal;
+    __syncthreads();
+    return res;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ count, uint32_t nb,
+                                                              uint32_t* __restrict__ bsum) {
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < nb) s += count[base + k];
+    uint32_t total;
+    block_excl_scan(s, &total);
+    if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* __restrict__ bsum, uint32_t nblocks) {
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < nblocks; base += blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const uint32_t v = i < nblocks ? bsum[i] : 0u;
+        uint32_t total;
+        const uint32_t ex = block_excl_scan(v, &total);
+        if (i < nblocks) bsum[i] = carry + ex;
+        carry += total;
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ count, uint32_t nb,
+                                                            const uint32_t* __restrict__ bsum,
+                                                            uint32_t* __restrict__ start,
+                                                            DevStatus* __restrict__ st) {
+    const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < nb ? count[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t total;
+    uint32_t run = block_excl_scan(s, &total) + bsum[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        const uint32_t b = base + k;
+        if (b < nb) {
+            start[b] = run;
+            count[b] = 0u;
+            if (b == nb - 1) {
+                // bucket nb-1 is the sentinel of removed particles
+                start[nb] = run + v[k];
+                st->n_sorted = run;
+                st->n_removed += v[k];
+            }
+        }
+        run += v[k];
+    }
+}
+
+// ---------------------------------------------------------------------
+// a2: scatter particle indices to their bucket slots (order within a
+// bucket is the atomics' order; the reorder fixes it).
+// ---------------------------------------------------------------------
+__global__ void __launch_bounds__(kBlock) k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
+                                                    const uint32_t* __restrict__ start,
+                                                    const DevStatus* __restrict__ st, uint32_t* __restrict__ unsorted) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        unsorted[start[key[i]] + slot[i]] = i;
+}
+
+// ---------------------------------------------------------------------
+// a3: one warp per cell.  Rank each particle of the cell by its unique key
+// (type, id) -> final slot; gather its data from the old arrays, re-base
+// the offset to the new cell (exact: Sterbenz), write the new arrays.
+// ---------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long sort_key(const float4* pos, const uint32_t* pid, uint32_t idx) {
+    const uint32_t bnd = __float_as_uint(pos[idx].w) >> 31;  // sign bit = boundary
+    return ((unsigned long long)bnd << 32) | pid[idx];
+}
+
+__global__ void __launch_bounds__(kBlock) k_reorder(
+    const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
+    const uint32_t* __restrict__ pinfo,
+    const uint32_t* __restrict__ pid, const uint32_t* __restrict__ start, const uint32_t* __restrict__ unsorted,
+    const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, float4* __restrict__ pos_o,
+    float4* __restrict__ vel_o, float* __restrict__ phat_o, uint32_t* __restrict__ cell_o,
+    uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->n_active = st->n_sorted;
+        st->max_neibs_seen = 0u;
+    }
+    for (uint32_t c = warp; c < n_cells; c += nwarps) {
+        const uint32_t beg = start[c], end = start[c + 1];
+        const uint32_t n = end - beg;
+        if (n == 0) continue;
+        for (uint32_t base = 0; base < n; base += 32) {
+            const uint32_t l = base + lane;
+            uint32_t idx = 0;
+            unsigned long long mine = ~0ull;
+            if (l < n) {
+                idx = unsorted[beg + l];
+                mine = sort_key(pos, pid, idx);
+            }
+            uint32_t rank = 0;
+            if (n <= 32) {
+                for (uint32_t k = 0; k < n; ++k) {
+                    const unsigned long long o = __shfl_sync(0xffffffffu, mine, (int)k);
+                    rank += o < mine;
+                }
+            } else {
+                for (uint32_t k = 0; k < n; ++k) {
+                    const unsigned long long o = sort_key(pos, pid, unsorted[beg + k]);
+                    rank += o < mine;
+                }
+            }
+            if (l < n) {
+                const uint32_t s = pinfo[idx];
+                const SceneDev& sc = scenes[s];
+                float4 p = pos[idx];
+                p.x -= (float)cell_shift(p.x, sc.inv_cell_f[0]) * sc.cell_f[0];
+                p.y -= (float)cell_shift(p.y, sc.inv_cell_f[1]) * sc.cell_f[1];
+                p.z -= (float)cell_shift(p.z, sc.inv_cell_f[2]) * sc.cell_f[2];
+                const uint32_t d = beg + rank;
+                pos_o[d] = p;
+                vel_o[d] = vel[idx];
+                phat_o[d] = phat[idx];
+                cell_o[d] = c;
+                pinfo_o[d] = s;
+                pid_o[d] = pid[idx];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// a5: split neighbour list (paper Section 4), one warp per cell.
+// Lanes hold the cell's particles (32 at a time); the particles of each of
+// the 27 neighbour cells are staged through shared memory 32 at a time and
+// every lane tests every staged candidate (shared-memory broadcast), so the
+// warp walks one candidate stream without divergence (the paper's
+// warp-per-cell build with shared-memory staging, Section 7).  Within a cell
+// particles are sorted fluid-first; a warp whose lanes are all boundary
+// particles (they need fluid neighbours only: boundary-boundary pairs carry
+// no interaction) stops each staged chunk at its fluid candidates.
+// ---------------------------------------------------------------------
+constexpr int kBuildWarps = 4;
+
+__global__ void __launch_bounds__(kBuildWarps * 32) k_build(
+    const float4* __restrict__ pos, const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ start,
+    const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, uint32_t* __restrict__ nlist,
+    uint32_t* __restrict__ ncount, float R2, uint32_t max_neibs, uint32_t stride) {
+    __shared__ float4 stage[kBuildWarps][32];
+    const int lane = threadIdx.x & 31;
+    const int wib = threadIdx.x >> 5;
+    const uint32_t nwarps = gridDim.x * kBuildWarps;
+    for (uint32_t c = blockIdx.x * kBuildWarps + wib; c < n_cells; c += nwarps) {
+        const uint32_t b0 = start[c], e0 = start[c + 1];
+        if (b0 == e0) continue;
+        const SceneDev& sc = scenes[pinfo[b0]];
+        int cx, cy, cz;
+        decode_local(c - sc.cell_offset, sc, cx, cy, cz);
+        for (uint32_t base = b0; base < e0; base += 32) {
+            const uint32_t i = base + lane;
+            const bool active = i < e0;
+            const float4 pi = active ? pos[i] : make_float4(0.f, 0.f, 0.f, -1.f);
+            const bool fluid_i = active && pi.w > 0.f;
+            const bool all_bnd = __all_sync(0xffffffffu, !fluid_i);
+            uint32_t nfw = 0, nbw = 0, nfound = 0;
+            for (int dz = -1; dz <= 1; ++dz) {
+                int z = cz + dz;
+                if (z < 0 || z >= sc.ncell[2]) {
+                    if (!((sc.periodic >> 2) & 1u)) continue;
+                    z = z < 0 ? z + sc.ncell[2] : z - sc.ncell[2];
+                }
+                for (int dy = -1; dy <= 1; ++dy) {
+                    int y = cy + dy;
+                    if (y < 0 || y >= sc.ncell[1]) {
+                        if (!((sc.periodic >> 1) & 1u)) continue;
+                        y = y < 0 ? y + sc.ncell[1] : y - sc.ncell[1];
+                    }
+                    const uint32_t row = sc.cell_offset + (uint32_t)sc.ncell[0] * ((uint32_t)y + (uint32_t)sc.ncell[1] * (uint32_t)z);
+                    const float by = pi.y - (float)dy * sc.cell_f[1];
+                    const float bz = pi.z - (float)dz * sc.cell_f[2];
+                    for (int dx = -1; dx <= 1; ++dx) {
+                        int x = cx + dx;
+                        if (x < 0 || x >= sc.ncell[0]) {
+                            if (!(sc.periodic & 1u)) continue;
+                            x = x < 0 ? x + sc.ncell[0] : x - sc.ncell[0];
+                        }
+                        const uint32_t cc = row + (uint32_t)x;
+                        const uint32_t b = start[cc], e = start[cc + 1];
+                        const float bx = pi.x - (float)dx * sc.cell_f[0];
+                        const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
+                        for (uint32_t cb = b; cb < e; cb += 32) {
+                            const uint32_t j = cb + lane;
+                            const float4 q = j < e ? pos[j] : make_float4(0.f, 0.f, 0.f, -1.f);
+                            __syncwarp();
+                            stage[wib][lane] = q;
+                            __syncwarp();
+                            uint32_t cnt = min(32u, e - cb);
+                            if (all_bnd) cnt = __popc(__ballot_sync(0xffffffffu, j < e && q.w > 0.f));
+                            for (uint32_t kk = 0; kk < cnt; ++kk) {
+                                const float4 pj = stage[wib][kk];
+                                const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                                const bool fluid_j = pj.w > 0.f;
+                                if (active && r2 < R2 && r2 > 0.f && (fluid_i || fluid_j)) {
+                                    ++nfound;
+                                    if (nfw + nbw < max_neibs) {
+                                        const uint32_t entry = ((cb + kk) << kCodeBits) | code;
+                                        if (fluid_j) {
+                                            nlist[(size_t)nfw * stride + i] = entry;
+                                            ++nfw;
+                                        } else {
+                                            nlist[(size_t)(max_neibs - 1 - nbw) * stride + i] = entry;
+                                            ++nbw;
+                                        }
+                                    }
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (active) {
+                if (nfw + nbw < max_neibs) {
+                    nlist[(size_t)nfw * stride + i] = kMarker;
+                    nlist[(size_t)(max_neibs - 1 - nbw) * stride + i] = kMarker;
+                }
+                ncount[i] = nfw | (nbw << 16);
+                if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
+            }
+            const uint32_t m = __reduce_max_sync(0xffffffffu, active ? nfound : 0u);
+            const uint32_t wsum = __reduce_add_sync(0xffffffffu, active ? nfw + nbw : 0u);
+            if (lane == 0) {
+                atomicMax(&st->max_neibs_seen, m);
+                atomicAdd(&st->list_entries, (unsigned long long)wsum);
+            }
+        }
+    }
+}
+
+inline unsigned grid_for(uint32_t n, int block) {
+    uint32_t g = (n + block - 1) / block;
+    return g ? g : 1;
+}
+
+}  // namespace
+
+uint32_t scan_blocks(uint32_t n_buckets) { return (n_buckets + kScanTile - 1) / kScanTile; }
+
+void launch_hash(const Buffers& b, int cur, const Geometry& g, const Phys& ph, int do_dt, cudaStream_t st) {
+    (void)ph; (void)do_dt;
+    k_hash<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.pos[cur], b.cell[cur], b.pinfo[cur], b.scenes, b.status,
+                                                        b.key, b.slot, b.count, g.n_cells);
+}
+
+void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st) {
+    const uint32_t nb = g.n_cells + 1;
+    const uint32_t blocks = scan_blocks(nb);
+    k_scan_reduce<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum);
+    k_scan_bsums<<<1, 1024, 0, st>>>(b.bsum, blocks);
+    k_scan_down<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum, b.start, b.status);
+}
+
+void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
+    (void)cur;
+    k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted);
+}
+
+void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
+    const int nxt = cur ^ 1;
+    const uint32_t warps_per_block = kBlock / 32;
+    uint32_t blocks = (g.n_cells + warps_per_block - 1) / warps_per_block;
+    if (blocks == 0) blocks = 1;
+    k_reorder<<<blocks, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pinfo[cur], b.pid[cur], b.start,
+                                          b.unsorted, b.scenes, g.n_cells, b.status, b.pos[nxt], b.vel[nxt],
+                                          b.phat[nxt], b.cell[nxt], b.pinfo[nxt], b.pid[nxt]);
+}
+
+void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    uint32_t blocks = (g.n_cells + kBuildWarps - 1) / kBuildWarps;
+    if (blocks == 0) blocks = 1;
+    k_build<<<blocks, kBuildWarps * 32, 0, st>>>(b.pos[cur], b.pinfo[cur], b.start, b.scenes, g.n_cells, b.status,
+                                                  b.nlist, b.ncount, ph.R2, ph.max_neibs, ph.stride);
+}
+
+}  // namespace sphg

@@ -1,0 +1,758 @@
+// C ABI of the GB300 WCSPH hot path: context, buffers, upload/download,
+// step orchestration (CUDA graphs), counters.  The argument conventions of
+// every entry point are documented in include/sph.h.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "sph_internal.cuh"
+
+using namespace sphg;
+
+struct sph_ctx {
+    sph_params p{};
+    Phys ph{};
+    Geometry g{};
+    Buffers b{};
+    std::vector<SceneDev> scenes_h;
+    int cur = 0;
+    int device = 0;
+    uint32_t n_uploaded = 0;
+    bool uploaded = false;
+    bool need_dt0 = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    uint32_t graph_nodes = 0;
+    size_t staging_bytes = 0;
+};
+
+namespace {
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) {                                        \
+            std::fprintf(stderr, "sph: %s failed: %s (%s:%d)\n", #call, \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);   \
+            return SPH_ERR_CUDA;                                        \
+        }                                                               \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// ---------------------------------------------------------------------
+// Upload: FP64 absolute position -> (cell, FP32 offset from the cell
+// centre) per scene grid; type packed in the sign of pos.w.
+// ---------------------------------------------------------------------
+__global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float* __restrict__ vel,
+                         const float* __restrict__ delta, const float* __restrict__ mass,
+                         const uint8_t* __restrict__ type, const uint32_t* __restrict__ scene,
+                         const SceneDev* __restrict__ scenes, uint32_t n_scenes, float4* __restrict__ pos_o,
+                         float4* __restrict__ vel_o, float* __restrict__ phat_o, uint32_t* __restrict__ cell_o,
+                         uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o, DevStatus* __restrict__ st,
+                         const Phys ph) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t bad = 0;
+        const uint32_t s = scene ? scene[i] : 0u;
+        const uint8_t t = type[i];
+        const float m = mass[i];
+        if (s >= n_scenes || t > 1 || !(m > 0.f) || !isfinite(m)) bad |= kUpBadArg;
+        const SceneDev& sc = scenes[s < n_scenes ? s : 0];
+        int c[3];
+        float o[3];
+        for (int a = 0; a < 3; ++a) {
+            double x = pos[3 * i + a];
+            if (!isfinite(x)) {
+                bad |= kUpNonFinite;
+                x = sc.origin[a];
+            }
+            double L = sc.cell_d[a] * sc.ncell[a];
+            double rel = x - sc.origin[a];
+            if ((sc.periodic >> a) & 1u) rel -= L * floor(rel / L);
+            int k = (int)floor(rel / sc.cell_d[a]);
+            if ((sc.periodic >> a) & 1u) {
+                if (k >= sc.ncell[a]) k = sc.ncell[a] - 1;
+                if (k < 0) k = 0;
+            } else if (k < 0 || k >= sc.ncell[a]) {
+                bad |= kUpOutOfDomain;
+                k = 0;
+            }
+            c[a] = k;
+            o[a] = (float)(rel - (k + 0.5) * sc.cell_d[a]);
+        }
+        const bool fluid = t == 0;
+        float4 v = make_float4(0.f, 0.f, 0.f, delta[i]);
+        if (fluid) {
+            v.x = vel[3 * i];
+            v.y = vel[3 * i + 1];
+            v.z = vel[3 * i + 2];
+        }
+        if (!isfinite(v.x + v.y + v.z) || !isfinite(v.w) || !(v.w > -1.f)) bad |= kUpNonFinite;
+        if (bad) atomicOr(&st->upload_bits, bad);
+        pos_o[i] = make_float4(o[0], o[1], o[2], fluid ? m : -m);
+        vel_o[i] = v;
+        phat_o[i] = eos_phat(v.w, ph, sc.phat_coef);
+        cell_o[i] = sc.cell_offset + (uint32_t)c[0] + (uint32_t)sc.ncell[0] * ((uint32_t)c[1] + (uint32_t)sc.ncell[1] * (uint32_t)c[2]);
+        pinfo_o[i] = s < n_scenes ? s : 0;
+        pid_o[i] = i;
+    }
+}
+
+__global__ void k_set_status_n(DevStatus* st, uint32_t n) {
+    st->n_active = n;
+    st->n_sorted = n;
+    st->n_removed = 0;
+    st->max_neibs_seen = 0;
+    st->upload_bits = 0;
+    st->steps = 0ull;
+    st->list_entries = 0ull;
+}
+
+__global__ void k_reset_dyn(SceneDyn* dyn, uint32_t n_scenes) {
+    for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
+        dyn[s].dt = 0.f;
+        dyn[s].amax2_bits = 0u;
+        dyn[s].dt_d = 0.0;
+        dyn[s].time = 0.0;
+    }
+}
+
+__device__ __forceinline__ double wrap_periodic(double x, const SceneDev& sc, int a) {
+    if ((sc.periodic >> a) & 1u) {
+        const double L = sc.cell_d[a] * sc.ncell[a];
+        const double rel = x - sc.origin[a];
+        x = sc.origin[a] + (rel - L * floor(rel / L));
+    }
+    return x;
+}
+
+__global__ void k_download(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                           const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
+                           const uint32_t* __restrict__ pid, const SceneDev* __restrict__ scenes,
+                           const DevStatus* __restrict__ st, uint32_t n_up, double* __restrict__ pos_o,
+                           float* __restrict__ vel_o, float* __restrict__ delta_o) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t id = pid[i];
+        if (id >= n_up) continue;
+        const SceneDev& sc = scenes[pinfo[i]];
+        int c[3];
+        decode_local(cell[i] - sc.cell_offset, sc, c[0], c[1], c[2]);
+        const float4 p = pos[i];
+        const float4 v = vel[i];
+        const float o[3] = {p.x, p.y, p.z};
+        if (pos_o)
+            for (int a = 0; a < 3; ++a)
+                pos_o[3 * (size_t)id + a] = wrap_periodic(sc.origin[a] + (c[a] + 0.5) * sc.cell_d[a] + (double)o[a], sc, a);
+        if (vel_o) {
+            vel_o[3 * (size_t)id] = v.x;
+            vel_o[3 * (size_t)id + 1] = v.y;
+            vel_o[3 * (size_t)id + 2] = v.z;
+        }
+        if (delta_o) delta_o[id] = v.w;
+    }
+}
+
+__global__ void k_download_forces(const float4* __restrict__ force, const uint32_t* __restrict__ pid,
+                                  const DevStatus* __restrict__ st, uint32_t n_up, float* __restrict__ acc,
+                                  float* __restrict__ drho) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t id = pid[i];
+        if (id >= n_up) continue;
+        const float4 f = force[i];
+        acc[3 * (size_t)id] = f.x;
+        acc[3 * (size_t)id + 1] = f.y;
+        acc[3 * (size_t)id + 2] = f.z;
+        drho[id] = f.w;
+    }
+}
+
+__global__ void k_download_neighbors(const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
+                                     const uint32_t* __restrict__ pid, const DevStatus* __restrict__ st,
+                                     uint32_t n_up, uint32_t max_neibs, uint32_t stride,
+                                     uint32_t* __restrict__ counts, uint32_t* __restrict__ ids) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t id = pid[i];
+        if (id >= n_up) continue;
+        const uint32_t cnt = ncount[i];
+        const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        counts[2 * (size_t)id] = nf;
+        counts[2 * (size_t)id + 1] = nb;
+        uint32_t* out = ids + (size_t)id * max_neibs;
+        for (uint32_t k = 0; k < nf; ++k) out[k] = pid[nlist[(size_t)k * stride + i] >> kCodeBits];
+        for (uint32_t k = 0; k < nb; ++k)
+            out[nf + k] = pid[nlist[(size_t)(max_neibs - 1 - k) * stride + i] >> kCodeBits];
+    }
+}
+
+int scene_from(const sph_params& p, const double origin[3], const double size[3], uint32_t periodic, double c0,
+               uint32_t cell_offset, SceneDev& s, uint64_t& ncells) {
+    const double R = p.kernel_radius * p.h;
+    ncells = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (!(size[a] > 0.0) || !std::isfinite(size[a]) || !std::isfinite(origin[a])) return SPH_ERR_ARG;
+        double k = std::floor(size[a] / R);
+        if (k < 1) k = 1;
+        if (((periodic >> a) & 1u) && k < 3) return SPH_ERR_ARG;  // minimum image needs >= 3 cells
+        if (k > 1e6) return SPH_ERR_ARG;
+        s.ncell[a] = (int32_t)k;
+        s.origin[a] = origin[a];
+        s.cell_d[a] = size[a] / k;
+        s.cell_f[a] = (float)s.cell_d[a];
+        s.inv_cell_f[a] = (float)(1.0 / s.cell_d[a]);
+        ncells *= (uint64_t)k;
+    }
+    if (!(c0 > 0.0)) return SPH_ERR_ARG;
+    s.cell_offset = cell_offset;
+    s.periodic = periodic & 7u;
+    s.c0 = (float)c0;
+    const double B = p.rho0 * c0 * c0 / p.gamma;
+    s.phat_coef = (float)(B / (p.rho0 * p.rho0));
+    s.pi_coef = (float)(p.alpha * p.h * c0 / p.rho0);
+    double cap = p.h / c0;
+    if (p.visc_model == SPH_VISC_LAMINAR && p.nu > 0.0) cap = std::fmin(cap, p.h * p.h / p.nu);
+    s.dt_cap = p.cfl * cap;
+    return SPH_OK;
+}
+
+void free_cells(sph_ctx* c) {
+    cudaFree(c->b.count);
+    cudaFree(c->b.start);
+    cudaFree(c->b.bsum);
+    cudaFree(c->b.scenes);
+    cudaFree(c->b.dyn);
+    c->b.count = c->b.start = c->b.bsum = nullptr;
+    c->b.scenes = nullptr;
+    c->b.dyn = nullptr;
+}
+
+void drop_graphs(sph_ctx* c) {
+    for (auto& gexec : c->graph)
+        if (gexec) {
+            cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
+        }
+}
+
+int alloc_cells(sph_ctx* c) {
+    const uint32_t nb = c->g.n_cells + 1;
+    CK(cudaMalloc(&c->b.count, sizeof(uint32_t) * nb));
+    CK(cudaMemset(c->b.count, 0, sizeof(uint32_t) * nb));
+    CK(cudaMalloc(&c->b.start, sizeof(uint32_t) * (nb + 1)));
+    CK(cudaMemset(c->b.start, 0, sizeof(uint32_t) * (nb + 1)));
+    CK(cudaMalloc(&c->b.bsum, sizeof(uint32_t) * (scan_blocks(nb) + 1)));
+    CK(cudaMalloc(&c->b.scenes, sizeof(SceneDev) * c->g.n_scenes));
+    CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->g.n_scenes, cudaMemcpyHostToDevice));
+    CK(cudaMalloc(&c->b.dyn, sizeof(SceneDyn) * c->g.n_scenes));
+    CK(cudaMemset(c->b.dyn, 0, sizeof(SceneDyn) * c->g.n_scenes));
+    return SPH_OK;
+}
+
+int set_scene_table(sph_ctx* c, uint32_t n, const sph_scene* sc) {
+    std::vector<SceneDev> tab(n);
+    uint64_t off = 0;
+    for (uint32_t s = 0; s < n; ++s) {
+        uint64_t nc = 0;
+        int rc = scene_from(c->p, sc[s].origin, sc[s].size, sc[s].periodic_mask, sc[s].c0, (uint32_t)off, tab[s], nc);
+        if (rc) return rc;
+        off += nc;
+        if (off >= 0xF0000000ull) return SPH_ERR_ARG;
+    }
+    drop_graphs(c);
+    free_cells(c);
+    c->scenes_h = tab;
+    c->g.n_scenes = n;
+    c->g.n_cells = (uint32_t)off;
+    c->ph.n_scenes = n;
+    return alloc_cells(c);
+}
+
+// neighbour pipeline on buffer `cur` -> buffer cur^1 (sorted), then list
+void enqueue_sort(sph_ctx* c, cudaStream_t st) {
+    launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+    launch_scan(c->b, c->g, st);
+    launch_scatter(c->b, c->cur, c->g, st);
+    launch_reorder(c->b, c->cur, c->g, st);
+    c->cur ^= 1;
+}
+
+void enqueue_build(sph_ctx* c, cudaStream_t st) {
+    enqueue_sort(c, st);
+    launch_build(c->b, c->cur, c->g, c->ph, st);
+}
+
+void enqueue_step(sph_ctx* c, cudaStream_t st) {
+    launch_dt(c->b, c->g, c->ph, 1, st);
+    enqueue_build(c, st);
+    launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st);
+    launch_forces(c->b, c->cur, c->g, c->ph, kCorrect, 0, st);
+}
+
+int capture_graphs(sph_ctx* c) {
+    const int cur0 = c->cur;
+    for (int par = 0; par < 2; ++par) {
+        c->cur = par;
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+        enqueue_step(c, c->cap_stream);
+        CK(cudaStreamEndCapture(c->cap_stream, &gr));
+        size_t nn = 0;
+        cudaGraphGetNodes(gr, nullptr, &nn);
+        c->graph_nodes = (uint32_t)nn;
+        cudaError_t e = cudaGraphInstantiate(&c->graph[par], gr, 0);
+        cudaGraphDestroy(gr);
+        if (e != cudaSuccess) {
+            std::fprintf(stderr, "sph: graph instantiate failed: %s\n", cudaGetErrorString(e));
+            c->cur = cur0;
+            return SPH_ERR_CUDA;
+        }
+    }
+    c->cur = cur0;
+    return SPH_OK;
+}
+
+int error_from_bits(uint32_t bits) {
+    if (bits & SPH_EBIT_NEIB_OVERFLOW) return SPH_ERR_NEIB_OVERFLOW;
+    if (bits & SPH_EBIT_NONFINITE) return SPH_ERR_NONFINITE;
+    if (bits & SPH_EBIT_TIMEOUT) return SPH_ERR_TIMEOUT;
+    return SPH_OK;
+}
+
+inline unsigned grid_for(uint32_t n, int block) {
+    uint32_t g = (n + block - 1) / block;
+    return g ? g : 1;
+}
+
+int do_upload(sph_ctx* c, uint32_t n, const double* pos, const float* vel, const float* delta, const float* mass,
+              const uint8_t* type, const uint32_t* scene, cudaStream_t st) {
+    k_set_status_n<<<1, 1, 0, st>>>(c->b.status, n);
+    k_reset_dyn<<<1, 256, 0, st>>>(c->b.dyn, c->g.n_scenes);
+    if (n) {
+        k_upload<<<grid_for(n, 256), 256, 0, st>>>(n, pos, vel, delta, mass, type, scene, c->b.scenes, c->g.n_scenes,
+                                                    c->b.pos[c->cur], c->b.vel[c->cur], c->b.phat[c->cur],
+                                                    c->b.cell[c->cur], c->b.pinfo[c->cur], c->b.pid[c->cur],
+                                                    c->b.status, c->ph);
+    }
+    DevStatus hs;
+    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    if (hs.upload_bits) {
+        c->uploaded = false;
+        if (hs.upload_bits & kUpBadArg) return SPH_ERR_ARG;
+        if (hs.upload_bits & kUpNonFinite) return SPH_ERR_NONFINITE;
+        return SPH_ERR_OUT_OF_DOMAIN;
+    }
+    CK(cudaMemsetAsync(c->b.count, 0, sizeof(uint32_t) * (c->g.n_cells + 1), st));
+    enqueue_build(c, st);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    c->n_uploaded = n;
+    c->uploaded = true;
+    c->need_dt0 = true;
+    return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sph_strerror(int code) {
+    switch (code) {
+        case SPH_OK: return "ok";
+        case SPH_ERR_ARG: return "invalid argument";
+        case SPH_ERR_CUDA: return "CUDA runtime error";
+        case SPH_ERR_CAPACITY: return "particle count exceeds max_particles";
+        case SPH_ERR_NEIB_OVERFLOW: return "neighbour list overflow (max_neibs too small)";
+        case SPH_ERR_OUT_OF_DOMAIN: return "particle outside the domain";
+        case SPH_ERR_NONFINITE: return "non-finite value in the particle state";
+        case SPH_ERR_TIMEOUT: return "device wait timed out";
+        case SPH_ERR_STATE: return "call out of order";
+        default: return "unknown error";
+    }
+}
+
+int sph_create(const sph_params* p, sph_ctx** out) {
+    if (!p || !out) return SPH_ERR_ARG;
+    const double gm = p->gamma;
+    if (!(p->h > 0) || !(p->rho0 > 0) || !(p->c0 > 0) || !(gm >= 1 && gm <= 8 && gm == std::floor(gm)) ||
+        !(p->kernel_radius > 0) || !(p->cfl > 0) || p->max_particles == 0 || p->max_particles > kMaxParticles ||
+        p->max_neibs < 8 || p->max_neibs > 1024 || (p->visc_model != SPH_VISC_ARTIFICIAL && p->visc_model != SPH_VISC_LAMINAR) ||
+        !(p->alpha >= 0) || !(p->nu >= 0))
+        return SPH_ERR_ARG;
+    sph_ctx* c = new (std::nothrow) sph_ctx();
+    if (!c) return SPH_ERR_ARG;
+    c->p = *p;
+    c->p.n_scenes = 1;
+    cudaGetDevice(&c->device);
+    // physics constants
+    Phys& ph = c->ph;
+    const double h = p->h, R = p->kernel_radius * p->h;
+    ph.h = (float)h;
+    ph.inv_h = (float)(1.0 / h);
+    ph.R2 = (float)(R * R);
+    ph.aF = (float)(105.0 / (128.0 * 3.14159265358979323846 * h * h * h * h * h));
+    ph.rho0 = (float)p->rho0;
+    ph.inv_rho0 = (float)(1.0 / p->rho0);
+    ph.eps_h2 = (float)(0.01 * h * h);
+    ph.nu4 = (float)(4.0 * p->nu);
+    for (int a = 0; a < 3; ++a) ph.g[a] = (float)p->g[a];
+    const int gam = (int)gm;
+    double binom = 1.0;
+    for (int k = 1; k <= 8; ++k) {
+        binom = k <= gam ? binom * (gam - k + 1) / k : 0.0;
+        ph.coef[k - 1] = (float)binom;
+    }
+    ph.h_d = h;
+    ph.cfl = p->cfl;
+    ph.dt_fixed = p->dt_fixed;
+    ph.visc = p->visc_model;
+    ph.max_neibs = p->max_neibs;
+    const uint32_t cap = p->max_particles;
+    ph.stride = (uint32_t)align_up(cap, 32);
+    c->g.cap = cap;
+    sph_scene s0{};
+    for (int a = 0; a < 3; ++a) {
+        s0.origin[a] = p->origin[a];
+        s0.size[a] = p->size[a];
+    }
+    s0.periodic_mask = p->periodic_mask;
+    s0.c0 = p->c0;
+    int rc = set_scene_table(c, 1, &s0);
+    if (rc) {
+        sph_destroy(c);
+        return rc;
+    }
+    Buffers& b = c->b;
+    auto alloc = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
+    bool ok = true;
+    for (int k = 0; k < 2; ++k) {
+        ok = ok && alloc((void**)&b.pos[k], sizeof(float4) * cap) && alloc((void**)&b.vel[k], sizeof(float4) * cap) &&
+             alloc((void**)&b.phat[k], sizeof(float) * cap) &&
+             alloc((void**)&b.cell[k], sizeof(uint32_t) * cap) && alloc((void**)&b.pinfo[k], sizeof(uint32_t) * cap) &&
+             alloc((void**)&b.pid[k], sizeof(uint32_t) * cap);
+    }
+    ok = ok && alloc((void**)&b.pos_s, sizeof(float4) * cap) && alloc((void**)&b.vel_s, sizeof(float4) * cap) &&
+         alloc((void**)&b.phat_s, sizeof(float) * cap) &&
+         alloc((void**)&b.force, sizeof(float4) * cap) && alloc((void**)&b.key, sizeof(uint32_t) * cap) &&
+         alloc((void**)&b.slot, sizeof(uint32_t) * cap) && alloc((void**)&b.unsorted, sizeof(uint32_t) * cap) &&
+         alloc((void**)&b.nlist, sizeof(uint32_t) * (size_t)ph.stride * p->max_neibs) &&
+         alloc((void**)&b.ncount, sizeof(uint32_t) * cap) && alloc((void**)&b.status, sizeof(DevStatus));
+    c->staging_bytes = 64 * (size_t)cap + 4096;
+    ok = ok && alloc(&b.staging, c->staging_bytes);
+    ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        sph_destroy(c);
+        return SPH_ERR_CUDA;
+    }
+    cudaMemset(b.status, 0, sizeof(DevStatus));
+    cudaMemset(b.force, 0, sizeof(float4) * cap);
+    cudaMemset(b.ncount, 0, sizeof(uint32_t) * cap);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        sph_destroy(c);
+        return SPH_ERR_CUDA;
+    }
+    *out = c;
+    return SPH_OK;
+}
+
+int sph_set_scenes(sph_ctx* c, uint32_t n_scenes, const sph_scene* scenes) {
+    if (!c || !scenes || n_scenes == 0 || n_scenes > (1u << 24)) return SPH_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    int rc = set_scene_table(c, n_scenes, scenes);
+    if (rc) return rc;
+    c->p.n_scenes = n_scenes;
+    c->uploaded = false;
+    return SPH_OK;
+}
+
+int sph_upload(sph_ctx* c, uint32_t n, const double* pos, const float* vel, const float* delta, const float* mass,
+               const uint8_t* type, const uint32_t* scene, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (n > c->g.cap) return SPH_ERR_CAPACITY;
+    if (n && (!pos || !vel || !delta || !mass || !type)) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    // staging layout: pos f64 | vel f32 | delta | mass | scene u32 | type u8
+    char* base = (char*)c->b.staging;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base + off;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    double* dpos = (double*)take(sizeof(double) * 3 * n);
+    float* dvel = (float*)take(sizeof(float) * 3 * n);
+    float* ddel = (float*)take(sizeof(float) * n);
+    float* dmass = (float*)take(sizeof(float) * n);
+    uint32_t* dsc = scene ? (uint32_t*)take(sizeof(uint32_t) * n) : nullptr;
+    uint8_t* dty = (uint8_t*)take(n);
+    if (off > c->staging_bytes) return SPH_ERR_CAPACITY;
+    if (n) {
+        CK(cudaMemcpyAsync(dpos, pos, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dvel, vel, sizeof(float) * 3 * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(ddel, delta, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dmass, mass, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+        if (scene) CK(cudaMemcpyAsync(dsc, scene, sizeof(uint32_t) * n, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(dty, type, n, cudaMemcpyHostToDevice, st));
+    }
+    return do_upload(c, n, dpos, dvel, ddel, dmass, dty, dsc, st);
+}
+
+int sph_upload_device(sph_ctx* c, uint32_t n, const double* pos, const float* vel, const float* delta,
+                      const float* mass, const uint8_t* type, const uint32_t* scene, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (n > c->g.cap) return SPH_ERR_CAPACITY;
+    if (n && (!pos || !vel || !delta || !mass || !type)) return SPH_ERR_ARG;
+    return do_upload(c, n, pos, vel, delta, mass, type, scene, S(stream));
+}
+
+int sph_build_neighbors(sph_ctx* c, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    enqueue_build(c, S(stream));
+    CK(cudaGetLastError());
+    return SPH_OK;
+}
+
+int sph_forces(sph_ctx* c, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, S(stream));
+    CK(cudaGetLastError());
+    return SPH_OK;
+}
+
+int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    if (c->need_dt0) {
+        // dt0 from one forces call on the initial state (reading C7)
+        launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+        CK(cudaGetLastError());
+        c->need_dt0 = false;
+    }
+    if (!c->graph[0]) {
+        int rc = capture_graphs(c);
+        if (rc) return rc;
+    }
+    for (uint32_t s = 0; s < nsteps; ++s) {
+        CK(cudaGraphLaunch(c->graph[c->cur], st));
+        c->cur ^= 1;
+    }
+    return SPH_OK;
+}
+
+int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_ms) {
+    if (!c || !phase_ms) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    if (c->need_dt0) {
+        launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+        c->need_dt0 = false;
+    }
+    cudaEvent_t ev[9];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    int rc = SPH_OK;
+    for (uint32_t s = 0; s < nsteps && rc == SPH_OK; ++s) {
+        cudaEventRecord(ev[0], st);
+        launch_dt(c->b, c->g, c->ph, 1, st);
+        cudaEventRecord(ev[1], st);
+        launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+        cudaEventRecord(ev[2], st);
+        launch_scan(c->b, c->g, st);
+        cudaEventRecord(ev[3], st);
+        launch_scatter(c->b, c->cur, c->g, st);
+        cudaEventRecord(ev[4], st);
+        launch_reorder(c->b, c->cur, c->g, st);
+        c->cur ^= 1;
+        cudaEventRecord(ev[5], st);
+        launch_build(c->b, c->cur, c->g, c->ph, st);
+        cudaEventRecord(ev[6], st);
+        launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st);
+        cudaEventRecord(ev[7], st);
+        launch_forces(c->b, c->cur, c->g, c->ph, kCorrect, 0, st);
+        cudaEventRecord(ev[8], st);
+        if (cudaEventSynchronize(ev[8]) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            rc = SPH_ERR_CUDA;
+            break;
+        }
+        for (int k = 0; k < 8; ++k) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+            phase_ms[k] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return rc;
+}
+
+int sph_download(sph_ctx* c, uint32_t n, double* pos, float* vel, float* delta, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (n != c->n_uploaded) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    char* base = (char*)c->b.staging;
+    double* dpos = (double*)base;
+    float* dvel = (float*)(base + align_up(sizeof(double) * 3 * n, 256));
+    float* ddel = (float*)((char*)dvel + align_up(sizeof(float) * 3 * n, 256));
+    int rc = sph_download_device(c, n, dpos, dvel, ddel, stream);
+    if (rc) return rc;
+    if (n) {
+        if (pos) CK(cudaMemcpyAsync(pos, dpos, sizeof(double) * 3 * n, cudaMemcpyDeviceToHost, st));
+        if (vel) CK(cudaMemcpyAsync(vel, dvel, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st));
+        if (delta) CK(cudaMemcpyAsync(delta, ddel, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    DevStatus hs;
+    CK(cudaMemcpy(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost));
+    return error_from_bits(hs.error_bits);
+}
+
+int sph_download_device(sph_ctx* c, uint32_t n, double* pos, float* vel, float* delta, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (n != c->n_uploaded) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    if (n) {
+        if (pos) CK(cudaMemsetAsync(pos, 0xFF, sizeof(double) * 3 * n, st));
+        if (vel) CK(cudaMemsetAsync(vel, 0xFF, sizeof(float) * 3 * n, st));
+        if (delta) CK(cudaMemsetAsync(delta, 0xFF, sizeof(float) * n, st));
+        k_download<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.pos[c->cur], c->b.vel[c->cur], c->b.cell[c->cur],
+                                                             c->b.pinfo[c->cur], c->b.pid[c->cur], c->b.scenes,
+                                                             c->b.status, n, pos, vel, delta);
+        CK(cudaGetLastError());
+    }
+    return SPH_OK;
+}
+
+int sph_download_forces(sph_ctx* c, uint32_t n, float* acc, float* drho, void* stream) {
+    if (!c || !acc || !drho) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (n != c->n_uploaded) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    char* base = (char*)c->b.staging;
+    float* dacc = (float*)base;
+    float* ddr = (float*)(base + align_up(sizeof(float) * 3 * n, 256));
+    if (n) {
+        CK(cudaMemsetAsync(dacc, 0xFF, sizeof(float) * 3 * n, st));
+        CK(cudaMemsetAsync(ddr, 0xFF, sizeof(float) * n, st));
+        k_download_forces<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.force, c->b.pid[c->cur], c->b.status, n, dacc,
+                                                                    ddr);
+        CK(cudaGetLastError());
+        CK(cudaMemcpyAsync(acc, dacc, sizeof(float) * 3 * n, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(drho, ddr, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    return SPH_OK;
+}
+
+int sph_download_neighbors(sph_ctx* c, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream) {
+    if (!c || !counts || !ids) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (n != c->n_uploaded) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    if (n == 0) return SPH_OK;
+    const size_t nid = (size_t)n * c->p.max_neibs;
+    uint32_t *dcnt = nullptr, *dids = nullptr;
+    CK(cudaMalloc(&dcnt, sizeof(uint32_t) * 2 * n));
+    if (cudaMalloc(&dids, sizeof(uint32_t) * nid) != cudaSuccess) {
+        cudaFree(dcnt);
+        return SPH_ERR_CUDA;
+    }
+    cudaMemsetAsync(dcnt, 0, sizeof(uint32_t) * 2 * n, st);
+    cudaMemsetAsync(dids, 0xFF, sizeof(uint32_t) * nid, st);
+    k_download_neighbors<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.nlist, c->b.ncount, c->b.pid[c->cur],
+                                                                   c->b.status, n, c->p.max_neibs, c->ph.stride, dcnt,
+                                                                   dids);
+    cudaMemcpyAsync(counts, dcnt, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, st);
+    cudaMemcpyAsync(ids, dids, sizeof(uint32_t) * nid, cudaMemcpyDeviceToHost, st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    cudaFree(dcnt);
+    cudaFree(dids);
+    return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+int sph_get_stats(sph_ctx* c, sph_stats* out, void* stream) {
+    if (!c || !out) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    DevStatus hs;
+    SceneDyn d0;
+    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&d0, c->b.dyn, sizeof(d0), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::memset(out, 0, sizeof(*out));
+    out->n_active = hs.n_active;
+    out->n_removed = hs.n_removed;
+    out->max_neibs_seen = hs.max_neibs_seen;
+    out->error_bits = hs.error_bits;
+    out->steps = hs.steps;
+    out->dt = d0.dt_d;
+    out->time = d0.time;
+    out->n_cells = c->g.n_cells;
+    out->kernels_per_step = c->graph_nodes;
+    out->list_entries = hs.list_entries;
+    return error_from_bits(hs.error_bits);
+}
+
+int sph_get_scene_times(sph_ctx* c, double* dt, double* time, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    std::vector<SceneDyn> d(c->g.n_scenes);
+    CK(cudaMemcpyAsync(d.data(), c->b.dyn, sizeof(SceneDyn) * d.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (size_t s = 0; s < d.size(); ++s) {
+        if (dt) dt[s] = d[s].dt_d;
+        if (time) time[s] = d[s].time;
+    }
+    return SPH_OK;
+}
+
+int sph_clear_error(sph_ctx* c, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    CK(cudaMemsetAsync(&c->b.status->error_bits, 0, sizeof(uint32_t), S(stream)));
+    return SPH_OK;
+}
+
+int sph_sync(sph_ctx* c, void* stream) {
+    sph_stats s;
+    return sph_get_stats(c, &s, stream);
+}
+
+void sph_destroy(sph_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    drop_graphs(c);
+    free_cells(c);
+    Buffers& b = c->b;
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(b.pos[k]);
+        cudaFree(b.vel[k]);
+        cudaFree(b.phat[k]);
+        cudaFree(b.cell[k]);
+        cudaFree(b.pinfo[k]);
+        cudaFree(b.pid[k]);
+    }
+    cudaFree(b.pos_s);
+    cudaFree(b.vel_s);
+    cudaFree(b.phat_s);
+    cudaFree(b.force);
+    cudaFree(b.key);
+    cudaFree(b.slot);
+    cudaFree(b.unsorted);
+    cudaFree(b.nlist);
+    cudaFree(b.ncount);
+    cudaFree(b.status);
+    cudaFree(b.staging);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,160 @@
+// Internal definitions shared by the library's translation units.
+//
+// Data layout in HBM (all arrays sorted by (cell, type, id) after each
+// neighbour pipeline, capacity `cap` particles):
+//   pos4[i]  float4 (ox, oy, oz, +-m): offset from the centre of the
+//            particle's cell (cell-relative positions, paper Section 2.3:
+//            uniform FP32 accuracy without extended precision); w holds the
+//            mass, negated for boundary particles (type in the sign bit).
+//   vel4[i]  float4 (ux, uy, uz, delta): velocity and relative density
+//            delta = rho/rho0 - 1 (FP32 near rest keeps ~1e-7 relative
+//            accuracy in P, which absolute rho ~ 1000 would not).
+//   cell[i]  u32 global cell key (scene cell offset + linear cell index).
+//   pinfo[i] u32 scene index.   pid[i] u32 upload id.
+//   nlist    u32[max_neibs * stride], neighbour-major (entry k of particle i
+//            at k*stride + i, paper Section 4 "interleaved" layout); fluid
+//            neighbours from slot 0 up, boundary neighbours from slot
+//            max_neibs-1 down, 0xFFFFFFFF end markers.  Entry = j << 6 | code,
+//            code = 2 bits per axis of the cell delta (d+1), so the
+//            separation is x_ij = o_i - o_j - d * cell (periodic images too).
+//   ncount[i] u32 nf | nb << 16.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph.h"
+
+namespace sphg {
+
+constexpr uint32_t kMarker = 0xFFFFFFFFu;
+constexpr int kCodeBits = 6;
+constexpr uint32_t kMaxParticles = 1u << (32 - kCodeBits);
+
+struct SceneDev {
+    double origin[3];
+    double cell_d[3];        // cell side in FP64 (upload/download conversion)
+    float cell_f[3];         // cell side in FP32 (device geometry)
+    float inv_cell_f[3];
+    int32_t ncell[3];
+    uint32_t cell_offset;    // first global cell key of this scene
+    uint32_t periodic;       // bit mask
+    float c0;
+    float phat_coef;         // B / rho0^2: P/rho^2 = phat_coef * delta*poly(delta)/(1+delta)^2
+    float pi_coef;           // alpha*h*c0/rho0: Pi = -pi_coef * (u.x)/((r^2+0.01h^2)(1+(d_i+d_j)/2))
+    double dt_cap;           // cfl * min(h/c0, h^2/nu)
+};
+
+struct SceneDyn {
+    float dt;                // time step used by this step's integration (FP32)
+    uint32_t amax2_bits;     // float bits of max |a|^2 over fluid particles (atomicMax)
+    double dt_d;             // the same dt in FP64 (reported)
+    double time;             // simulated time
+};
+
+struct DevStatus {
+    uint32_t n_active;       // particles in the sorted arrays
+    uint32_t n_sorted;       // in-domain count found by the last scan
+    uint32_t n_removed;      // cumulative removed (left the domain)
+    uint32_t max_neibs_seen; // largest count of the last build
+    uint32_t error_bits;     // SPH_EBIT_*
+    uint32_t upload_bits;    // validation of the last upload
+    uint32_t pad[2];
+    unsigned long long steps;
+    unsigned long long list_entries;  // cumulative neighbour-list entries written
+};
+
+// upload validation bits
+constexpr uint32_t kUpBadArg = 1u, kUpOutOfDomain = 2u, kUpNonFinite = 4u;
+
+// Kernel-uniform physics, passed by value (lands in the constant bank).
+struct Phys {
+    float h, inv_h, R2;      // R2 = (kernel_radius*h)^2
+    float aF;                // F(q) = aF (q-2)^3, aF = 105/(128 pi h^5)
+    float rho0, inv_rho0;
+    float eps_h2;            // 0.01 h^2
+    float nu4;               // 4 nu
+    float g[3];
+    float coef[8];           // C(gamma,k), k = 1..8, zero-padded
+    double h_d, cfl, dt_fixed;
+    int visc;
+    uint32_t max_neibs;
+    uint32_t stride;         // neighbour-major stride (>= cap, multiple of 32)
+    uint32_t n_scenes;
+};
+
+// P/rho^2 of Cole's EOS from delta = rho/rho0 - 1 (binomial form, no
+// cancellation near rest): phat_coef * delta * sum_k C(gamma,k) delta^(k-1) / (1+delta)^2.
+// Stored per particle by every kernel that writes delta.
+__device__ __forceinline__ float eos_phat(float d, const Phys& ph, float phat_coef) {
+    float poly = ph.coef[7];
+#pragma unroll
+    for (int k = 6; k >= 0; --k) poly = fmaf(poly, d, ph.coef[k]);
+    const float opd = 1.0f + d;
+    return phat_coef * d * poly / (opd * opd);
+}
+
+// ---- cell helpers ------------------------------------------------------
+__device__ __forceinline__ int cell_shift(float o, float inv_cell) {
+    // number of cells the offset o has moved past the cell centre
+    return (int)floorf(fmaf(o, inv_cell, 0.5f));
+}
+
+__device__ __forceinline__ void decode_local(uint32_t local, const SceneDev& s, int& cx, int& cy, int& cz) {
+    const uint32_t nx = (uint32_t)s.ncell[0], ny = (uint32_t)s.ncell[1];
+    cx = (int)(local % nx);
+    const uint32_t r = local / nx;
+    cy = (int)(r % ny);
+    cz = (int)(r / ny);
+}
+
+__device__ __forceinline__ uint32_t encode_entry(uint32_t j, int dx, int dy, int dz) {
+    return (j << kCodeBits) | (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
+}
+
+// ---- launch wrappers (host side) --------------------------------------
+struct Buffers {
+    float4* pos[2];
+    float4* vel[2];
+    uint32_t* cell[2];
+    uint32_t* pinfo[2];
+    uint32_t* pid[2];
+    float* phat[2];          // P/rho^2 per particle, same order as pos/vel
+    float4* pos_s;           // predicted state
+    float4* vel_s;
+    float* phat_s;
+    float4* force;           // (ax, ay, az, drho) of sph_forces
+    uint32_t* key;           // new cell key per particle (hash)
+    uint32_t* slot;          // rank within the new cell at hash time (unordered)
+    uint32_t* count;         // per bucket counts (n_cells + 1 buckets)
+    uint32_t* start;         // exclusive scan (n_cells + 2 entries)
+    uint32_t* bsum;          // scan block sums
+    uint32_t* unsorted;      // particle index per sorted slot before the in-cell sort
+    uint32_t* nlist;
+    uint32_t* ncount;
+    SceneDev* scenes;
+    SceneDyn* dyn;
+    DevStatus* status;
+    void* staging;           // upload/download staging (64 B per particle)
+};
+
+struct Geometry {
+    uint32_t cap;
+    uint32_t n_cells;        // over all scenes (the sentinel bucket is n_cells)
+    uint32_t n_scenes;
+};
+
+// neighbours.cu
+void launch_hash(const Buffers& b, int cur, const Geometry& g, const Phys& ph, int do_dt, cudaStream_t st);
+void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st);
+void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
+uint32_t scan_blocks(uint32_t n_buckets);
+
+// forces.cu
+enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };
+void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
+                   int acc_dt, cudaStream_t st);
+void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st);
+
+}  // namespace sphg

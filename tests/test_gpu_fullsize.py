@@ -1,0 +1,70 @@
+"""Parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (marked gpu).  The oracle computes sampled particles one by
+one: forces of a seeded sample of 3000 particles, neighbour counts, and the
+state after one full step.
+
+  dam_break_1M : tank 1.6 x 0.67 x 0.6 m, column 0.4 x 0.67 x 0.3 m, dp 4.3 mm (1.65M particles)
+  dam_break_16M: same at dp 4.3 mm / 16^(1/3)                             (~20.5M particles)
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_11328_gb300 import scenes
+from tests.gpu_common import rel_check, require_gpu, sim_for
+
+pytestmark = pytest.mark.gpu
+TOL_RHS = 1e-5
+
+
+@pytest.fixture(autouse=True, scope="module")
+def _gpu():
+    require_gpu()
+
+
+def _sample(n, k, seed):
+    return np.sort(np.random.default_rng(seed).choice(n, size=min(k, n), replace=False)).astype(np.int32)
+
+
+def _check_sample(s, sim, sample):
+    sim.forces()
+    acc, drho = sim.download_forces()
+    a_ref, d_ref, nnb, mag = oracle.rhs_sample(oracle.params(s), s.pos, s.vel, s.delta, s.mass, s.ptype, sample)
+    ra, fa = rel_check(acc[sample], a_ref, TOL_RHS, f"{s.name} acceleration", mag[:, 0])
+    rd, fd = rel_check(drho[sample], d_ref, TOL_RHS, f"{s.name} density rate", mag[:, 1])
+    cond = mag[:, 0] / np.maximum(np.linalg.norm(a_ref, axis=1), 1e-300)
+    print(f"{s.name}: acceleration max rel {ra:.2e} ({100 * fa:.2f}% within 1e-5, max condition {cond.max():.0f}); "
+          f"density rate max rel {rd:.2e} ({100 * fd:.2f}%)")
+    return nnb
+
+
+@pytest.mark.parametrize("dp,name", [(4.3e-3, "dam_break_1M"), (4.3e-3 / 16 ** (1 / 3), "dam_break_16M")])
+def test_fullsize_forces_sampled(dp, name):
+    s = scenes.dam_break(dp=dp, name=name)
+    sim = sim_for(s)
+    st = sim.stats()
+    assert st["n_active"] == s.n and st["error_bits"] == 0
+    sample = _sample(s.n, 3000, 11)
+    nnb = _check_sample(s, sim, sample)
+    # fluid particles: the GPU list holds every neighbour (no pair sits in the
+    # cutoff band on this lattice: |r - 2h| >= 0.1 dp for all lattice pairs)
+    counts = sim.download_neighbors()[0] if s.n < 5_000_000 else None
+    if counts is not None:
+        f = s.ptype[sample] == 0
+        assert np.array_equal(counts[sample][f].sum(1), nnb[f])
+
+
+def test_fullsize_one_step_sampled():
+    s = scenes.dam_break(dp=4.3e-3)
+    sim = sim_for(s)
+    sim.step(1)
+    pos, vel, delta = sim.download()
+    x1, u1, d1, _, dts = oracle.step(oracle.params(s), s.pos, s.vel, s.delta, s.mass, s.ptype, 1)
+    assert sim.stats()["dt"] == pytest.approx(dts[0], rel=1e-5)
+    du, du_ref = vel - s.vel, u1 - s.vel
+    scale = np.max(np.abs(du_ref))
+    assert np.max(np.abs(du - du_ref)) <= 1e-4 * scale + 4 * np.spacing(np.float32(scale))
+    dd, dd_ref = delta - s.delta, d1 - s.delta
+    assert np.max(np.abs(dd - dd_ref)) <= 1e-4 * np.max(np.abs(dd_ref)) + 4 * np.spacing(np.float32(0.02))
+    half_cell = 0.5 * max(s.size[a] / np.floor(s.size[a] / (2 * s.h)) for a in range(3))
+    assert np.max(np.abs(pos - x1)) <= 1e-4 * np.max(np.abs(x1 - s.pos)) + 2 * np.spacing(np.float32(half_cell))
