@@ -185,6 +185,25 @@ int sph_download_forces(sph_ctx* ctx, uint32_t n, float* acc, float* drho, void*
  * HOST arrays; synchronises. */
 int sph_download_neighbors(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream);
 
+/* Same result as sph_download_neighbors, without allocating device memory.
+ * The paper has no counterpart: this entry point exists for callers that
+ * must not call cudaMalloc/cudaFree while they run, e.g. a process whose
+ * device memory is already held by another allocator (a framework's caching
+ * allocator), or a loop that cannot afford the device-wide synchronisation
+ * cudaMalloc and cudaFree may cause.  The device staging sph_download_neighbors
+ * allocates per call lives here in one fixed device array of 24 MiB that
+ * every GPU loading the library holds until the process exits.
+ * Limits: n <= 2^20 particles and n * max_neibs <= 2^22 entries, else
+ * SPH_ERR_CAPACITY (nothing is done).  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents (this call clears what it reads
+ * back), so calls that overlap on the GPU (other streams, other threads)
+ * race and must be serialised by the caller.  The current device must be the
+ * context's device (else SPH_ERR_STATE).  HOST output arrays as in
+ * sph_download_neighbors; synchronises `stream`. */
+int sph_download_neighbors_noalloc(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream);
+
 /* Read device counters into *out (synchronises `stream`).  Returns the
  * sticky device error as a code (SPH_ERR_NEIB_OVERFLOW, SPH_ERR_NONFINITE,
  * SPH_ERR_TIMEOUT) if one is set, else SPH_OK; *out is filled either way. */

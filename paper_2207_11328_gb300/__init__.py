@@ -77,6 +77,7 @@ _SIGS = {
     "sph_download_device": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
     "sph_download_forces": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
     "sph_download_neighbors": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
+    "sph_download_neighbors_noalloc": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
     "sph_get_stats": [_vp, ctypes.POINTER(Stats), _vp],
     "sph_get_scene_times": [_vp, _vp, _vp, _vp],
     "sph_clear_error": [_vp, _vp],
@@ -242,6 +243,17 @@ class Simulation:
         ids = np.empty((n, mn), np.uint32)
         _check(_lib().sph_download_neighbors(self._h, n, _ptr(counts), _ptr(ids), _stream_handle(stream)),
                "sph_download_neighbors")
+        return counts, ids
+
+    def download_neighbors_noalloc(self, stream=None):
+        """download_neighbors without device allocation (fixed library-owned
+        staging; n <= 2^20 and n * max_neibs <= 2^22)."""
+        n = self.n
+        mn = self.params.max_neibs
+        counts = np.empty((n, 2), np.uint32)
+        ids = np.empty((n, mn), np.uint32)
+        _check(_lib().sph_download_neighbors_noalloc(self._h, n, _ptr(counts), _ptr(ids), _stream_handle(stream)),
+               "sph_download_neighbors_noalloc")
         return counts, ids
 
     # ---- the hot path ------------------------------------------------------

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -678,6 +679,71 @@ int sph_download_neighbors(sph_ctx* c, uint32_t n, uint32_t* counts, uint32_t* i
     cudaFree(dcnt);
     cudaFree(dids);
     return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------------
+// Allocation-free neighbour download.  Same kernel and outputs as
+// sph_download_neighbors, but the device staging lives in one file-scope
+// device array instead of buffers from cudaMalloc, for callers that must not
+// allocate device memory at call time.  The array is held by every device
+// that loads the library until the process exits; all calls share it.
+// ---------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocMaxParticles = size_t(1) << 20;  // counts: 2 u32 per particle
+constexpr size_t kNoAllocMaxEntries = size_t(1) << 22;    // ids: n * max_neibs u32
+// [counts: 2 * kNoAllocMaxParticles][ids: kNoAllocMaxEntries]  (24 MiB)
+static __device__ __align__(256) uint32_t g_noalloc_scratch[2 * kNoAllocMaxParticles + kNoAllocMaxEntries];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+uint32_t* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side name of a __device__ array is not a device address).
+int noalloc_scratch(uint32_t** out) {
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return SPH_ERR_ARG;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_ptr[dev] = static_cast<uint32_t*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SPH_OK;
+}
+
+}  // namespace
+
+int sph_download_neighbors_noalloc(sph_ctx* c, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream) {
+    if (!c || !counts || !ids) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (n != c->n_uploaded) return SPH_ERR_ARG;
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != c->device) return SPH_ERR_STATE;
+    const size_t nid = (size_t)n * c->p.max_neibs;
+    if ((size_t)n > kNoAllocMaxParticles || nid > kNoAllocMaxEntries) return SPH_ERR_CAPACITY;
+    if (n == 0) return SPH_OK;
+    uint32_t* scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    uint32_t* dcnt = scratch;
+    uint32_t* dids = scratch + 2 * kNoAllocMaxParticles;
+    cudaStream_t st = S(stream);
+    // the array keeps the previous call's contents: reset the parts this call reads back
+    CK(cudaMemsetAsync(dcnt, 0, sizeof(uint32_t) * 2 * n, st));
+    CK(cudaMemsetAsync(dids, 0xFF, sizeof(uint32_t) * nid, st));
+    k_download_neighbors<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.nlist, c->b.ncount, c->b.pid[c->cur],
+                                                                   c->b.status, n, c->p.max_neibs, c->ph.stride, dcnt,
+                                                                   dids);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(counts, dcnt, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(ids, dids, sizeof(uint32_t) * nid, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return SPH_OK;
 }
 
 int sph_get_stats(sph_ctx* c, sph_stats* out, void* stream) {
