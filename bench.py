@@ -51,6 +51,24 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def forces_traffic(workload):
+    """Measured DRAM bytes per force launch (mean of the two passes) from the
+    committed ncu summary, or None when forces.cu changed since the capture."""
+    import glob
+    import hashlib
+    src = os.path.join(ROOT, "paper_2207_11328_gb300", "csrc", "forces.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    for path in glob.glob(os.path.join(ROOT, "profiles", "forces_traffic_*.md")):
+        kv = {}
+        for line in open(path):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("workload") == workload and kv.get("source_sha256") == sha:
+            return 0.5 * (float(kv["predictor_dram_bytes"]) + float(kv["corrector_dram_bytes"]))
+    return None
+
+
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
@@ -278,19 +296,11 @@ def run_ours(args, world, rank, local):
     t_pred = phases["forces_predict"] / args.profile_steps / 1e3
     t_corr = phases["forces_correct"] / args.profile_steps / 1e3
     achieved = (b_pred + b_corr) / (t_pred + t_corr) / 1e9
-    traffic = None
-    tr_path = os.path.join(ROOT, "profiles", "forces_traffic.json")
-    if os.path.exists(tr_path):
-        try:
-            with open(tr_path) as f:
-                tr = json.load(f)
-            if tr.get("workload") == args.workload:
-                traffic = tr.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = forces_traffic(args.workload)
     roofline = {"bound": "hbm", "kernel": "forces (predictor + corrector passes)", "achieved": achieved,
                 "peak": hbm, "peak_source": f"{peak_src} HBM copy bandwidth", "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
+                "algorithmic_bytes_per_launch": 0.5 * (b_pred + b_corr),
                 "algorithmic_bytes_per_step": b_pred + b_corr,
                 "phase_ms_per_step": {k: v / args.profile_steps for k, v in phases.items()}}
 
