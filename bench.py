@@ -259,6 +259,7 @@ def run_ours(args, world, rank, local):
     scene, wdesc = make_workload(args.workload)
     stream = torch.cuda.current_stream()
     sim = Simulation.from_scene(scene, max_neibs=args.max_neibs, stream=stream)
+    tuned = sim.autotune(stream=stream)
     sim.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     st0 = sim.stats(stream=stream)
@@ -309,7 +310,8 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wdesc, "n_particles": scene.n, "n_fluid": scene.n_fluid, "dp": scene.dp,
                        "h": scene.h, "max_neibs": args.max_neibs, "rebuild": "every step",
-                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}"},
+                       "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
+                       "autotuned": {"build": tuned[0], "forces_block": tuned[1]}},
             "particle_steps_per_s": psteps, "mean_neighbours": entries / max(1.0, psteps_local),
             "roofline": roofline, "gpu_launches": int(kernels * args.steps),
             "clocks": clk.summary()}

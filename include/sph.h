@@ -158,6 +158,19 @@ int sph_forces(sph_ctx* ctx, void* stream);
  * for the next step.  Replays a captured CUDA graph per step. */
 int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
 
+/* Autotuner (launch shapes only; results are unchanged): times each
+ * neighbour-build variant (one thread per particle with 128 or 256 threads
+ * per block, or one warp per cell with 2, 4 or 8 cells per block) and the
+ * force kernels at 64, 128 and 256 threads per block on the uploaded state
+ * (3 timed launches each, CUDA events on `stream`), keeps the fastest and
+ * re-captures the step graph on the next sph_step.  Outputs (nullable): the
+ * chosen build variant (see sph_build_variant_name) and force block size.
+ * Synchronises `stream`; SPH_ERR_STATE before an upload. */
+int sph_autotune(sph_ctx* ctx, void* stream, int* build_variant, int* forces_block);
+
+/* Name of a neighbour-build variant of sph_autotune (static storage). */
+const char* sph_build_variant_name(int variant);
+
 /* Same work as sph_step, launched kernel by kernel (no graph) with CUDA
  * events recorded on `stream` between the launches; adds the elapsed
  * milliseconds of each phase to phase_ms[0..7]: 0 dt, 1 hash, 2 scan,

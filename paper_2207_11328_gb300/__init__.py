@@ -82,6 +82,8 @@ _SIGS = {
     "sph_get_scene_times": [_vp, _vp, _vp, _vp],
     "sph_clear_error": [_vp, _vp],
     "sph_sync": [_vp, _vp],
+    "sph_autotune": [_vp, _vp, _vp, _vp],
+    "sph_build_variant_name": [ctypes.c_int],
     "sph_strerror": [ctypes.c_int],
     "sph_destroy": [_vp],
 }
@@ -103,6 +105,7 @@ def _lib():
             fn.argtypes = args
             fn.restype = ctypes.c_int
         lib.sph_strerror.restype = ctypes.c_char_p
+        lib.sph_build_variant_name.restype = ctypes.c_char_p
         lib.sph_destroy.restype = None
         _LIB = lib
     return _LIB
@@ -265,6 +268,15 @@ class Simulation:
 
     def step(self, nsteps=1, stream=None):
         _check(_lib().sph_step(self._h, int(nsteps), _stream_handle(stream)), "sph_step")
+
+    def autotune(self, stream=None):
+        """Pick the fastest neighbour-build variant and force block size on the
+        uploaded state; returns (build variant name, force threads per block)."""
+        v = ctypes.c_int()
+        fb = ctypes.c_int()
+        _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fb)),
+               "sph_autotune")
+        return _lib().sph_build_variant_name(v.value).decode(), fb.value
 
     PHASES = ("dt", "hash", "scan", "scatter", "reorder", "build", "forces_predict", "forces_correct")
 

@@ -25,8 +25,6 @@ namespace sphg {
 
 namespace {
 
-constexpr int kBlock = 128;
-
 __device__ __forceinline__ float cell_delta(uint32_t bits2, float cell) {
     // bits2 = d + 1 in {0, 1, 2}  ->  d * cell
     return bits2 == 0u ? -cell : (bits2 == 2u ? cell : 0.0f);
@@ -79,7 +77,7 @@ __device__ __forceinline__ void fluid_pair(uint32_t e, const float4& pi, const f
     }
 }
 
-template <int VISC, int MODE>
+template <int VISC, int MODE, int kBlock>
 __global__ void __launch_bounds__(kBlock) k_forces(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
@@ -100,12 +98,27 @@ __global__ void __launch_bounds__(kBlock) k_forces(
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
+            // list entries come from DRAM: load four slots ahead of their use
+            const size_t S = ph.stride;
             const uint32_t* lp = nlist + i;
-#pragma unroll 2
-            for (uint32_t k = 0; k < nf; ++k, lp += ph.stride)
+            uint32_t k = 0;
+            for (; k + 4 <= nf; k += 4, lp += 4 * S) {
+                const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
+                fluid_pair<VISC, false>(e0, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, false>(e1, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, false>(e2, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, false>(e3, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+            }
+            for (; k < nf; ++k, lp += S)
                 fluid_pair<VISC, false>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-            lp = nlist + (size_t)(ph.max_neibs - 1) * ph.stride + i;
-            for (uint32_t k = 0; k < nb; ++k, lp -= ph.stride)
+            lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
+            k = 0;
+            for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
+                const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
+                fluid_pair<VISC, true>(e0, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, true>(e1, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+            }
+            for (; k < nb; ++k, lp -= S)
                 fluid_pair<VISC, true>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
             acc.ax += ph.g[0];
             acc.ay += ph.g[1];
@@ -206,26 +219,36 @@ __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__
     if (threadIdx.x == 0 && advance) st->steps += 1ull;
 }
 
+template <int VISC, int B>
+void launch_forces_b(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
+                     cudaStream_t st) {
+    const unsigned grid = g.cap ? (g.cap + B - 1) / B : 1;
+    switch (mode) {
+        case kForcesOnly:
+            k_forces<VISC, kForcesOnly, B><<<grid, B, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr,
+                                                                nullptr, b.force, b.pinfo[cur], b.nlist, b.ncount,
+                                                                b.scenes, b.dyn, b.status, ph, acc_dt);
+            break;
+        case kPredict:
+            k_forces<VISC, kPredict, B><<<grid, B, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s,
+                                                             b.phat_s, nullptr, b.pinfo[cur], b.nlist, b.ncount,
+                                                             b.scenes, b.dyn, b.status, ph, 0);
+            break;
+        case kCorrect:
+            k_forces<VISC, kCorrect, B><<<grid, B, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur],
+                                                             b.phat[cur], nullptr, b.pinfo[cur], b.nlist, b.ncount,
+                                                             b.scenes, b.dyn, b.status, ph, 0);
+            break;
+    }
+}
+
 template <int VISC>
 void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
                      cudaStream_t st) {
-    const unsigned grid = g.cap ? (g.cap + kBlock - 1) / kBlock : 1;
-    switch (mode) {
-        case kForcesOnly:
-            k_forces<VISC, kForcesOnly><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr,
-                                                                  nullptr, b.force, b.pinfo[cur], b.nlist, b.ncount,
-                                                                  b.scenes, b.dyn, b.status, ph, acc_dt);
-            break;
-        case kPredict:
-            k_forces<VISC, kPredict><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s,
-                                                               b.phat_s, nullptr, b.pinfo[cur], b.nlist, b.ncount,
-                                                               b.scenes, b.dyn, b.status, ph, 0);
-            break;
-        case kCorrect:
-            k_forces<VISC, kCorrect><<<grid, kBlock, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur],
-                                                               b.phat[cur], nullptr, b.pinfo[cur], b.nlist, b.ncount,
-                                                               b.scenes, b.dyn, b.status, ph, 0);
-            break;
+    switch (ph.forces_block) {
+        case 64: launch_forces_b<VISC, 64>(b, cur, g, ph, mode, acc_dt, st); break;
+        case 256: launch_forces_b<VISC, 256>(b, cur, g, ph, mode, acc_dt, st); break;
+        default: launch_forces_b<VISC, 128>(b, cur, g, ph, mode, acc_dt, st); break;
     }
 }
 

@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ pid, const uint32_t* __restrict__ start, const uint32_t* __restrict__ unsorted,
-    const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, float4* __restrict__ pos_o,
+    const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, uint32_t* __restrict__ cell_nfluid,
+    float4* __restrict__ pos_o,
     float4* __restrict__ vel_o, float* __restrict__ phat_o, uint32_t* __restrict__ cell_o,
     uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o) {
     const int lane = threadIdx.x & 31;
@@ -193,7 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
     for (uint32_t c = warp; c < n_cells; c += nwarps) {
         const uint32_t beg = start[c], end = start[c + 1];
         const uint32_t n = end - beg;
-        if (n == 0) continue;
+        uint32_t nfluid = 0;
         for (uint32_t base = 0; base < n; base += 32) {
             const uint32_t l = base + lane;
             uint32_t idx = 0;
@@ -202,6 +203,7 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
                 idx = unsorted[beg + l];
                 mine = sort_key(pos, pid, idx);
             }
+            nfluid += __popc(__ballot_sync(0xffffffffu, l < n && (mine >> 32) == 0ull));
             uint32_t rank = 0;
             if (n <= 32) {
                 for (uint32_t k = 0; k < n; ++k) {
@@ -230,94 +232,169 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
                 pid_o[d] = pid[idx];
             }
         }
+        if (lane == 0) cell_nfluid[c] = nfluid;
     }
 }
 
 // ---------------------------------------------------------------------
-// a5: split neighbour list (paper Section 4), one warp per cell.
-// Lanes hold the cell's particles (32 at a time); the particles of each of
-// the 27 neighbour cells are staged through shared memory 32 at a time and
-// every lane tests every staged candidate (shared-memory broadcast), so the
-// warp walks one candidate stream without divergence (the paper's
-// warp-per-cell build with shared-memory staging, Section 7).  Within a cell
-// particles are sorted fluid-first; a warp whose lanes are all boundary
-// particles (they need fluid neighbours only: boundary-boundary pairs carry
-// no interaction) stops each staged chunk at its fluid candidates.
+// a5: split neighbour list (paper Section 4), one warp per cell (the paper's
+// warp-per-cell build, Section 7).  The warp first stages every candidate of
+// the 27-cell neighbourhood into shared memory: its position already shifted
+// into the frame of the central cell (o_j + d*cell) and its list entry
+// (j << 6 | cell-delta code).  Lanes hold the cell's particles (32 at a time)
+// and each lane tests the whole flat candidate array (shared-memory
+// broadcast, no per-cell control flow in the inner loop).  Within a cell
+// particles are sorted fluid-first; boundary particles keep only fluid
+// neighbours (boundary-boundary pairs carry no interaction), and a warp of
+// boundary particles only stages fluid candidates.
 // ---------------------------------------------------------------------
-constexpr int kBuildWarps = 4;
+constexpr int kStage = 256;  // staged candidates per warp and window (multiple of 32)
 
-__global__ void __launch_bounds__(kBuildWarps * 32) k_build(
+template <int kBuildWarps>
+__global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_cell(
     const float4* __restrict__ pos, const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ start,
-    const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, uint32_t* __restrict__ nlist,
-    uint32_t* __restrict__ ncount, float R2, uint32_t max_neibs, uint32_t stride) {
-    __shared__ float4 stage[kBuildWarps][32];
+    const uint32_t* __restrict__ cell_nfluid, const SceneDev* __restrict__ scenes, uint32_t n_cells,
+    DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,
+    uint32_t max_neibs, uint32_t stride) {
+    __shared__ float4 sq[kBuildWarps][kStage];
+    __shared__ uint32_t se[kBuildWarps][kStage];
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
+    float4* const q_s = sq[wib];
+    uint32_t* const e_s = se[wib];
     const uint32_t nwarps = gridDim.x * kBuildWarps;
     for (uint32_t c = blockIdx.x * kBuildWarps + wib; c < n_cells; c += nwarps) {
         const uint32_t b0 = start[c], e0 = start[c + 1];
         if (b0 == e0) continue;
         const SceneDev& sc = scenes[pinfo[b0]];
+        // a cell of boundary particles only needs the fluid candidates (first in each cell)
+        const bool all_bnd = cell_nfluid[c] == 0;
         int cx, cy, cz;
         decode_local(c - sc.cell_offset, sc, cx, cy, cz);
+        // lane k < 27: neighbour cell k = (dx, dy, dz), its candidate range and exclusive offset
+        uint32_t kb = 0, kn = 0;
+        {
+            const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+            int nc[3] = {cx + dx, cy + dy, cz + dz};
+            bool ok = lane < 27;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                if (nc[a] < 0 || nc[a] >= sc.ncell[a]) {
+                    if ((sc.periodic >> a) & 1u)
+                        nc[a] = nc[a] < 0 ? nc[a] + sc.ncell[a] : nc[a] - sc.ncell[a];
+                    else
+                        ok = false;
+                }
+            }
+            if (ok) {
+                const uint32_t cc = sc.cell_offset + (uint32_t)nc[0] +
+                                    (uint32_t)sc.ncell[0] * ((uint32_t)nc[1] + (uint32_t)sc.ncell[1] * (uint32_t)nc[2]);
+                kb = start[cc];
+                kn = all_bnd ? cell_nfluid[cc] : start[cc + 1] - kb;
+            }
+        }
+        uint32_t koff = kn;  // inclusive scan over lanes -> exclusive offsets
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, koff, o);
+            if (lane >= o) koff += t;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, koff, 31);
+        koff -= kn;
+        if (total == 0) {
+            for (uint32_t base = b0; base < e0; base += 32) {
+                const uint32_t i = base + lane;
+                if (i < e0) {
+                    nlist[i] = kMarker;
+                    nlist[(size_t)(max_neibs - 1) * stride + i] = kMarker;
+                    ncount[i] = 0u;
+                }
+            }
+            continue;
+        }
         for (uint32_t base = b0; base < e0; base += 32) {
             const uint32_t i = base + lane;
             const bool active = i < e0;
             const float4 pi = active ? pos[i] : make_float4(0.f, 0.f, 0.f, -1.f);
             const bool fluid_i = active && pi.w > 0.f;
-            const bool all_bnd = __all_sync(0xffffffffu, !fluid_i);
+            // parked lanes sit far away on one side, padding candidates on the other
+            const float px = active ? pi.x : 3.0e18f, py = pi.y, pz = pi.z;
             uint32_t nfw = 0, nbw = 0, nfound = 0;
-            for (int dz = -1; dz <= 1; ++dz) {
-                int z = cz + dz;
-                if (z < 0 || z >= sc.ncell[2]) {
-                    if (!((sc.periodic >> 2) & 1u)) continue;
-                    z = z < 0 ? z + sc.ncell[2] : z - sc.ncell[2];
-                }
-                for (int dy = -1; dy <= 1; ++dy) {
-                    int y = cy + dy;
-                    if (y < 0 || y >= sc.ncell[1]) {
-                        if (!((sc.periodic >> 1) & 1u)) continue;
-                        y = y < 0 ? y + sc.ncell[1] : y - sc.ncell[1];
+            uint32_t* pf = nlist + i;                                     // next fluid slot
+            uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;  // next boundary slot
+            for (uint32_t w0 = 0; w0 < total; w0 += kStage) {
+                const uint32_t w1 = min(total, w0 + (uint32_t)kStage);
+                __syncwarp();
+                for (int k = 0; k < 27; ++k) {
+                    const uint32_t b = __shfl_sync(0xffffffffu, kb, k);
+                    const uint32_t n = __shfl_sync(0xffffffffu, kn, k);
+                    const uint32_t off = __shfl_sync(0xffffffffu, koff, k);
+                    if (off >= w1 || off + n <= w0) continue;
+                    const int dx = k % 3 - 1, dy = (k / 3) % 3 - 1, dz = k / 9 - 1;
+                    const float shx = (float)dx * sc.cell_f[0], shy = (float)dy * sc.cell_f[1],
+                                shz = (float)dz * sc.cell_f[2];
+                    const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
+                    const uint32_t t0 = off < w0 ? w0 - off : 0u;
+                    const uint32_t t1 = min(n, w1 - off);
+                    for (uint32_t t = t0 + lane; t < t1; t += 32) {
+                        const uint32_t j = b + t;
+                        float4 q = pos[j];
+                        q.x += shx;
+                        q.y += shy;
+                        q.z += shz;
+                        q_s[off + t - w0] = q;
+                        e_s[off + t - w0] = (j << kCodeBits) | code;
                     }
-                    const uint32_t row = sc.cell_offset + (uint32_t)sc.ncell[0] * ((uint32_t)y + (uint32_t)sc.ncell[1] * (uint32_t)z);
-                    const float by = pi.y - (float)dy * sc.cell_f[1];
-                    const float bz = pi.z - (float)dz * sc.cell_f[2];
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        int x = cx + dx;
-                        if (x < 0 || x >= sc.ncell[0]) {
-                            if (!(sc.periodic & 1u)) continue;
-                            x = x < 0 ? x + sc.ncell[0] : x - sc.ncell[0];
+                }
+                const uint32_t cnt = w1 - w0;
+                const uint32_t padded = (cnt + 31u) & ~31u;
+                if (cnt + lane < padded) q_s[cnt + lane] = make_float4(-3.0e18f, 0.f, 0.f, 1.f);
+                __syncwarp();
+                for (uint32_t kb32 = 0; kb32 < padded; kb32 += 32) {
+                    // fluid candidates of this block (uniform), then branch-free distance tests
+                    const uint32_t fmask = __ballot_sync(0xffffffffu, q_s[kb32 + lane].w > 0.f);
+                    uint32_t hits = 0;
+#pragma unroll
+                    for (int u = 0; u < 32; ++u) {
+                        const float4 q = q_s[kb32 + u];
+                        const float rx = px - q.x, ry = py - q.y, rz = pz - q.z;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        hits |= (uint32_t)(r2 < R2 && r2 > 0.f) << u;
+                    }
+                    uint32_t hf = hits & fmask;
+                    uint32_t hb = fluid_i ? hits & ~fmask : 0u;
+                    const uint32_t cf = __popc(hf), cb = __popc(hb);
+                    nfound += cf + cb;
+                    if (nfw + nbw + cf + cb <= max_neibs) {
+                        nfw += cf;
+                        nbw += cb;
+                        while (hf) {
+                            const int u = __ffs(hf) - 1;
+                            hf &= hf - 1u;
+                            *pf = e_s[kb32 + u];
+                            pf += stride;
                         }
-                        const uint32_t cc = row + (uint32_t)x;
-                        const uint32_t b = start[cc], e = start[cc + 1];
-                        const float bx = pi.x - (float)dx * sc.cell_f[0];
-                        const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
-                        for (uint32_t cb = b; cb < e; cb += 32) {
-                            const uint32_t j = cb + lane;
-                            const float4 q = j < e ? pos[j] : make_float4(0.f, 0.f, 0.f, -1.f);
-                            __syncwarp();
-                            stage[wib][lane] = q;
-                            __syncwarp();
-                            uint32_t cnt = min(32u, e - cb);
-                            if (all_bnd) cnt = __popc(__ballot_sync(0xffffffffu, j < e && q.w > 0.f));
-                            for (uint32_t kk = 0; kk < cnt; ++kk) {
-                                const float4 pj = stage[wib][kk];
-                                const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
-                                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                                const bool fluid_j = pj.w > 0.f;
-                                if (active && r2 < R2 && r2 > 0.f && (fluid_i || fluid_j)) {
-                                    ++nfound;
-                                    if (nfw + nbw < max_neibs) {
-                                        const uint32_t entry = ((cb + kk) << kCodeBits) | code;
-                                        if (fluid_j) {
-                                            nlist[(size_t)nfw * stride + i] = entry;
-                                            ++nfw;
-                                        } else {
-                                            nlist[(size_t)(max_neibs - 1 - nbw) * stride + i] = entry;
-                                            ++nbw;
-                                        }
-                                    }
-                                }
+                        while (hb) {
+                            const int u = __ffs(hb) - 1;
+                            hb &= hb - 1u;
+                            *pb = e_s[kb32 + u];
+                            pb -= stride;
+                        }
+                    } else {
+                        // list full: keep the first hits in candidate order, count the rest
+                        uint32_t h = hf | hb;
+                        while (h) {
+                            const int u = __ffs(h) - 1;
+                            h &= h - 1u;
+                            if (nfw + nbw >= max_neibs) break;
+                            if ((fmask >> u) & 1u) {
+                                *pf = e_s[kb32 + u];
+                                pf += stride;
+                                ++nfw;
+                            } else {
+                                *pb = e_s[kb32 + u];
+                                pb -= stride;
+                                ++nbw;
                             }
                         }
                     }
@@ -325,8 +402,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build(
             }
             if (active) {
                 if (nfw + nbw < max_neibs) {
-                    nlist[(size_t)nfw * stride + i] = kMarker;
-                    nlist[(size_t)(max_neibs - 1 - nbw) * stride + i] = kMarker;
+                    *pf = kMarker;
+                    *pb = kMarker;
                 }
                 ncount[i] = nfw | (nbw << 16);
                 if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
@@ -337,6 +414,95 @@ __global__ void __launch_bounds__(kBuildWarps * 32) k_build(
                 atomicMax(&st->max_neibs_seen, m);
                 atomicAdd(&st->list_entries, (unsigned long long)wsum);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------
+// a5, second variant: one thread per particle (the paper's baseline
+// build, Section 7).  Lanes of a warp are consecutive particles of ~2 cells
+// and read the same candidates (L1 broadcast).  Candidates are fluid-first
+// in each cell (cell_nfluid), so a boundary particle walks only the fluid
+// part of each neighbour cell and types need no per-candidate test.
+// ---------------------------------------------------------------------
+template <int kBlockT>
+__global__ void __launch_bounds__(kBlockT) k_build_tpp(
+    const float4* __restrict__ pos, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
+    const uint32_t* __restrict__ start, const uint32_t* __restrict__ cell_nfluid, const SceneDev* __restrict__ scenes,
+    DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,
+    uint32_t max_neibs, uint32_t stride) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const SceneDev& sc = scenes[pinfo[i]];
+        const float4 pi = pos[i];
+        const bool fluid_i = pi.w > 0.f;
+        int cx, cy, cz;
+        decode_local(cell[i] - sc.cell_offset, sc, cx, cy, cz);
+        uint32_t nfw = 0, nbw = 0, nfound = 0;
+        uint32_t* pf = nlist + i;
+        uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;
+        for (int dz = -1; dz <= 1; ++dz) {
+            int z = cz + dz;
+            if (z < 0 || z >= sc.ncell[2]) {
+                if (!((sc.periodic >> 2) & 1u)) continue;
+                z = z < 0 ? z + sc.ncell[2] : z - sc.ncell[2];
+            }
+            for (int dy = -1; dy <= 1; ++dy) {
+                int y = cy + dy;
+                if (y < 0 || y >= sc.ncell[1]) {
+                    if (!((sc.periodic >> 1) & 1u)) continue;
+                    y = y < 0 ? y + sc.ncell[1] : y - sc.ncell[1];
+                }
+                const uint32_t row = sc.cell_offset + (uint32_t)sc.ncell[0] * ((uint32_t)y + (uint32_t)sc.ncell[1] * (uint32_t)z);
+                const float by = pi.y - (float)dy * sc.cell_f[1];
+                const float bz = pi.z - (float)dz * sc.cell_f[2];
+                for (int dx = -1; dx <= 1; ++dx) {
+                    int x = cx + dx;
+                    if (x < 0 || x >= sc.ncell[0]) {
+                        if (!(sc.periodic & 1u)) continue;
+                        x = x < 0 ? x + sc.ncell[0] : x - sc.ncell[0];
+                    }
+                    const uint32_t cc = row + (uint32_t)x;
+                    const uint32_t b = start[cc];
+                    const uint32_t ef = b + cell_nfluid[cc];             // end of the fluid part
+                    const uint32_t e = fluid_i ? start[cc + 1] : ef;
+                    const float bx = pi.x - (float)dx * sc.cell_f[0];
+                    const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
+                    for (uint32_t j = b; j < e; ++j) {
+                        const float4 pj = pos[j];
+                        const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        if (r2 < R2 && r2 > 0.f) {
+                            ++nfound;
+                            if (nfw + nbw < max_neibs) {
+                                const uint32_t entry = (j << kCodeBits) | code;
+                                if (j < ef) {
+                                    *pf = entry;
+                                    pf += stride;
+                                    ++nfw;
+                                } else {
+                                    *pb = entry;
+                                    pb -= stride;
+                                    ++nbw;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (nfw + nbw < max_neibs) {
+            *pf = kMarker;
+            *pb = kMarker;
+        }
+        ncount[i] = nfw | (nbw << 16);
+        if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
+        const unsigned mask = __activemask();
+        const uint32_t m = __reduce_max_sync(mask, nfound);
+        const uint32_t wsum = __reduce_add_sync(mask, nfw + nbw);
+        if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1)) {
+            atomicMax(&st->max_neibs_seen, m);
+            atomicAdd(&st->list_entries, (unsigned long long)wsum);
         }
     }
 }
@@ -375,15 +541,39 @@ void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t s
     uint32_t blocks = (g.n_cells + warps_per_block - 1) / warps_per_block;
     if (blocks == 0) blocks = 1;
     k_reorder<<<blocks, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pinfo[cur], b.pid[cur], b.start,
-                                          b.unsorted, b.scenes, g.n_cells, b.status, b.pos[nxt], b.vel[nxt],
+                                          b.unsorted, b.scenes, g.n_cells, b.status, b.cell_nfluid, b.pos[nxt], b.vel[nxt],
                                           b.phat[nxt], b.cell[nxt], b.pinfo[nxt], b.pid[nxt]);
 }
 
-void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
-    uint32_t blocks = (g.n_cells + kBuildWarps - 1) / kBuildWarps;
+template <int W>
+void launch_build_cell(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    uint32_t blocks = (g.n_cells + W - 1) / W;
     if (blocks == 0) blocks = 1;
-    k_build<<<blocks, kBuildWarps * 32, 0, st>>>(b.pos[cur], b.pinfo[cur], b.start, b.scenes, g.n_cells, b.status,
-                                                  b.nlist, b.ncount, ph.R2, ph.max_neibs, ph.stride);
+    k_build_cell<W><<<blocks, W * 32, 0, st>>>(b.pos[cur], b.pinfo[cur], b.start, b.cell_nfluid, b.scenes, g.n_cells,
+                                                b.status, b.nlist, b.ncount, ph.R2, ph.max_neibs, ph.stride);
+}
+
+template <int B>
+void launch_build_tpp(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    k_build_tpp<B><<<grid_for(g.cap, B), B, 0, st>>>(b.pos[cur], b.cell[cur], b.pinfo[cur], b.start, b.cell_nfluid,
+                                                     b.scenes, b.status, b.nlist, b.ncount, ph.R2, ph.max_neibs,
+                                                     ph.stride);
+}
+
+const char* build_variant_name(int v) {
+    static const char* names[kBuildVariants] = {"thread/particle x128", "thread/particle x256", "warp/cell x2 cells/CTA",
+                                                "warp/cell x4 cells/CTA", "warp/cell x8 cells/CTA"};
+    return v >= 0 && v < kBuildVariants ? names[v] : "?";
+}
+
+void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    switch (ph.build_variant) {
+        case 0: launch_build_tpp<128>(b, cur, g, ph, st); break;
+        case 1: launch_build_tpp<256>(b, cur, g, ph, st); break;
+        case 2: launch_build_cell<2>(b, cur, g, ph, st); break;
+        case 3: launch_build_cell<4>(b, cur, g, ph, st); break;
+        default: launch_build_cell<8>(b, cur, g, ph, st); break;
+    }
 }
 
 }  // namespace sphg

@@ -226,9 +226,10 @@ void free_cells(sph_ctx* c) {
     cudaFree(c->b.count);
     cudaFree(c->b.start);
     cudaFree(c->b.bsum);
+    cudaFree(c->b.cell_nfluid);
     cudaFree(c->b.scenes);
     cudaFree(c->b.dyn);
-    c->b.count = c->b.start = c->b.bsum = nullptr;
+    c->b.count = c->b.start = c->b.bsum = c->b.cell_nfluid = nullptr;
     c->b.scenes = nullptr;
     c->b.dyn = nullptr;
 }
@@ -248,6 +249,8 @@ int alloc_cells(sph_ctx* c) {
     CK(cudaMalloc(&c->b.start, sizeof(uint32_t) * (nb + 1)));
     CK(cudaMemset(c->b.start, 0, sizeof(uint32_t) * (nb + 1)));
     CK(cudaMalloc(&c->b.bsum, sizeof(uint32_t) * (scan_blocks(nb) + 1)));
+    CK(cudaMalloc(&c->b.cell_nfluid, sizeof(uint32_t) * nb));
+    CK(cudaMemset(c->b.cell_nfluid, 0, sizeof(uint32_t) * nb));
     CK(cudaMalloc(&c->b.scenes, sizeof(SceneDev) * c->g.n_scenes));
     CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->g.n_scenes, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->b.dyn, sizeof(SceneDyn) * c->g.n_scenes));
@@ -415,6 +418,8 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.dt_fixed = p->dt_fixed;
     ph.visc = p->visc_model;
     ph.max_neibs = p->max_neibs;
+    ph.build_variant = 0;
+    ph.forces_block = 128;
     const uint32_t cap = p->max_particles;
     ph.stride = (uint32_t)align_up(cap, 32);
     c->g.cap = cap;
@@ -550,6 +555,62 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
     }
     return SPH_OK;
 }
+
+int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_block) {
+    if (!c) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_ms = [&](auto&& launch) -> float {
+        launch();  // warm
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 3; ++r) launch();
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        return ms / 3.f;
+    };
+    // neighbour build: thread/particle (128, 256 threads) or warp/cell (2, 4, 8 cells per CTA);
+    // all variants write the same list, so the state is unchanged by tuning
+    int best_v = c->ph.build_variant;
+    float best = 3.4e38f;
+    for (int v = 0; v < kBuildVariants; ++v) {
+        c->ph.build_variant = v;
+        const float ms = time_ms([&] { launch_build(c->b, c->cur, c->g, c->ph, st); });
+        if (ms < best) {
+            best = ms;
+            best_v = v;
+        }
+    }
+    c->ph.build_variant = best_v;
+    launch_build(c->b, c->cur, c->g, c->ph, st);
+    // force kernels: threads per block
+    const int blocks[3] = {64, 128, 256};
+    int best_b = c->ph.forces_block;
+    best = 3.4e38f;
+    for (int k = 0; k < 3; ++k) {
+        c->ph.forces_block = blocks[k];
+        const float ms = time_ms([&] { launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, st); });
+        if (ms < best) {
+            best = ms;
+            best_b = blocks[k];
+        }
+    }
+    c->ph.forces_block = best_b;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    drop_graphs(c);  // captured launches carry the old shapes
+    if (build_variant) *build_variant = best_v;
+    if (forces_block) *forces_block = best_b;
+    return SPH_OK;
+}
+
+const char* sph_build_variant_name(int variant) { return build_variant_name(variant); }
 
 int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_ms) {
     if (!c || !phase_ms) return SPH_ERR_ARG;

@@ -80,7 +80,12 @@ struct Phys {
     uint32_t max_neibs;
     uint32_t stride;         // neighbour-major stride (>= cap, multiple of 32)
     uint32_t n_scenes;
+    int build_variant;       // neighbour-build kernel variant (autotuned), see build_variant_name
+    int forces_block;        // threads per block of the force kernels (autotuned)
 };
+
+constexpr int kBuildVariants = 5;
+const char* build_variant_name(int v);
 
 // P/rho^2 of Cole's EOS from delta = rho/rho0 - 1 (binomial form, no
 // cancellation near rest): phat_coef * delta * sum_k C(gamma,k) delta^(k-1) / (1+delta)^2.
@@ -127,6 +132,7 @@ struct Buffers {
     uint32_t* slot;          // rank within the new cell at hash time (unordered)
     uint32_t* count;         // per bucket counts (n_cells + 1 buckets)
     uint32_t* start;         // exclusive scan (n_cells + 2 entries)
+    uint32_t* cell_nfluid;   // fluid particles per cell (they come first in the cell)
     uint32_t* bsum;          // scan block sums
     uint32_t* unsorted;      // particle index per sorted slot before the in-cell sort
     uint32_t* nlist;

@@ -128,3 +128,22 @@ def test_deterministic_bitwise():
         sim.close()
     for a, b in zip(*outs):
         assert np.array_equal(a, b)
+
+
+def test_autotune_keeps_results_bitwise():
+    # every build variant writes the same list, every block size the same sums
+    s = _small_dam(dp=0.03)
+    sim = sim_for(s)
+    sim.forces()
+    a0, d0 = sim.download_forces()
+    c0 = sim.download_neighbors()
+    variant, block = sim.autotune()
+    assert block in (64, 128, 256) and variant
+    sim.build_neighbors()
+    sim.forces()
+    a1, d1 = sim.download_forces()
+    c1 = sim.download_neighbors()
+    assert np.array_equal(a0, a1) and np.array_equal(d0, d1)
+    assert np.array_equal(c0[0], c1[0]) and np.array_equal(c0[1], c1[1])
+    sim.step(3)
+    assert sim.stats()["steps"] == 3
