@@ -158,6 +158,39 @@ int sph_forces(sph_ctx* ctx, void* stream);
  * for the next step.  Replays a captured CUDA graph per step. */
 int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
 
+/* ---- differentiable run (reverse mode) --------------------------------
+ * Loss L on the state after T steps; gradients w.r.t. the initial state and
+ * the artificial-viscosity coefficient alpha.  The paper has no adjoint; it
+ * differentiates the step of Section 2.1 with readings C1-C7 as implemented
+ * here, with dt frozen (no gradient through dt) and the neighbour list of
+ * each step held fixed within the step (F and F' vanish at the cutoff, so
+ * the step map is C1 across list changes). */
+
+/* Set alpha (artificial viscosity only; SPH_ERR_ARG otherwise).  Host call,
+ * synchronises the device; invalidates a recording. */
+int sph_set_alpha(sph_ctx* ctx, double alpha);
+
+/* Forward of a differentiable run: T predictor-corrector steps from the
+ * uploaded state with dt frozen at params.dt_fixed, or (if that is <= 0) at
+ * the CFL dt of one forces call on the initial state (*dt_out, nullable),
+ * storing a checkpoint of the state every K steps (T % K == 0).  One scene
+ * only.  Allocates its checkpoints and tape (about 48 B per particle per
+ * checkpoint, ~180 B per particle per step of one segment).  Afterwards
+ * the context holds the state after T steps.  Synchronises `stream`. */
+int sph_record(sph_ctx* ctx, uint32_t T, uint32_t K, void* stream, double* dt_out);
+
+/* Reverse of the last sph_record.  Inputs: DEVICE arrays in upload order
+ * with the adjoints of the final state, dL/dx_T (n*3), dL/du_T (n*3),
+ * dL/ddelta_T (n); any may be NULL (zero).  Outputs: DEVICE arrays dL/dx_0,
+ * dL/du_0 (n*3), dL/ddelta_0 (n), nullable; *alphabar (host, nullable) =
+ * dL/dalpha.  Boundary particles' x and u are constants (zero adjoint).
+ * Each segment of K steps is recomputed from its checkpoint and reversed
+ * step by step; the vector-Jacobian products are gathers over the
+ * symmetric neighbour lists (deterministic, no atomics).  Leaves the
+ * context at the recorded initial state.  Synchronises `stream`. */
+int sph_backward(sph_ctx* ctx, const float* xbar_T, const float* ubar_T, const float* dbar_T, float* xbar_0,
+                 float* ubar_0, float* dbar_0, double* alphabar, void* stream);
+
 /* Autotuner (launch shapes only; results are unchanged): times each
  * neighbour-build variant (one thread per particle with 128 or 256 threads
  * per block, or one warp per cell with 2, 4 or 8 cells per block) and the

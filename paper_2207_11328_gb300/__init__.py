@@ -83,6 +83,9 @@ _SIGS = {
     "sph_clear_error": [_vp, _vp],
     "sph_sync": [_vp, _vp],
     "sph_autotune": [_vp, _vp, _vp, _vp],
+    "sph_set_alpha": [_vp, ctypes.c_double],
+    "sph_record": [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp],
+    "sph_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "sph_build_variant_name": [ctypes.c_int],
     "sph_strerror": [ctypes.c_int],
     "sph_destroy": [_vp],
@@ -277,6 +280,33 @@ class Simulation:
         _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fb)),
                "sph_autotune")
         return _lib().sph_build_variant_name(v.value).decode(), fb.value
+
+    # ---- differentiable run ---------------------------------------------------
+    def set_alpha(self, alpha):
+        _check(_lib().sph_set_alpha(self._h, float(alpha)), "sph_set_alpha")
+
+    def record(self, T, K, stream=None):
+        """T steps with frozen dt and a checkpoint every K steps; returns dt."""
+        dt = ctypes.c_double()
+        _check(_lib().sph_record(self._h, int(T), int(K), _stream_handle(stream), ctypes.byref(dt)), "sph_record")
+        return dt.value
+
+    def backward(self, xbar_T=None, ubar_T=None, dbar_T=None, want_x=False, want_delta=False, stream=None):
+        """Adjoint of the last record: torch CUDA float32 inputs (n,3)/(n,) or None;
+        returns (dL/dx0 or None, dL/du0, dL/ddelta0 or None, dL/dalpha)."""
+        import torch
+        n = self.n
+        dev = torch.device("cuda", torch.cuda.current_device())
+        p = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())  # noqa: E731
+        for t in (xbar_T, ubar_T, dbar_T):
+            assert t is None or (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous())
+        ubar0 = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        xbar0 = torch.empty((n, 3), dtype=torch.float32, device=dev) if want_x else None
+        dbar0 = torch.empty((n,), dtype=torch.float32, device=dev) if want_delta else None
+        ab = ctypes.c_double()
+        _check(_lib().sph_backward(self._h, p(xbar_T), p(ubar_T), p(dbar_T), p(xbar0), p(ubar0), p(dbar0),
+                                   ctypes.byref(ab), _stream_handle(stream)), "sph_backward")
+        return xbar0, ubar0, dbar0, ab.value
 
     PHASES = ("dt", "hash", "scan", "scatter", "reorder", "build", "forces_predict", "forces_correct")
 

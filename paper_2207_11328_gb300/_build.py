@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsph_gb300.so")
 OBJDIR = os.path.join(ROOT, "_build")
-SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu"]
+SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -12,7 +12,22 @@
 
 using namespace sphg;
 
+// Recording of a differentiable run: checkpoints of the pre-step state every
+// K steps and a per-step tape of one segment, re-filled during the backward.
+struct AdjTape {
+    bool valid = false;
+    uint32_t T = 0, K = 0, n = 0;
+    double dt = 0.0;
+    Phys ph_rec{};
+    std::vector<char*> ckpt;   // T/K checkpoints (pos4 vel4 phat cell pinfo pid)
+    char* steps = nullptr;     // K records (sorted state, predicted state, start, cell_nfluid)
+    size_t ckpt_bytes = 0, step_bytes = 0;
+    sphg::AdjBuffers a{};
+    void* adj_mem = nullptr;
+};
+
 struct sph_ctx {
+    AdjTape tape;
     sph_params p{};
     Phys ph{};
     Geometry g{};
@@ -216,6 +231,7 @@ int scene_from(const sph_params& p, const double origin[3], const double size[3]
     const double B = p.rho0 * c0 * c0 / p.gamma;
     s.phat_coef = (float)(B / (p.rho0 * p.rho0));
     s.pi_coef = (float)(p.alpha * p.h * c0 / p.rho0);
+    s.pi_unit = (float)(p.h * c0 / p.rho0);
     double cap = p.h / c0;
     if (p.visc_model == SPH_VISC_LAMINAR && p.nu > 0.0) cap = std::fmin(cap, p.h * p.h / p.nu);
     s.dt_cap = p.cfl * cap;
@@ -418,6 +434,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.dt_fixed = p->dt_fixed;
     ph.visc = p->visc_model;
     ph.max_neibs = p->max_neibs;
+    ph.gamma_i = (int)gm;
     ph.build_variant = 0;
     ph.forces_block = 128;
     const uint32_t cap = p->max_particles;
@@ -611,6 +628,204 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_block
 }
 
 const char* sph_build_variant_name(int variant) { return build_variant_name(variant); }
+
+namespace {
+
+void free_tape(sph_ctx* c) {
+    AdjTape& t = c->tape;
+    for (char* p : t.ckpt) cudaFree(p);
+    t.ckpt.clear();
+    cudaFree(t.steps);
+    cudaFree(t.adj_mem);
+    t.steps = nullptr;
+    t.adj_mem = nullptr;
+    t.valid = false;
+}
+
+// copy the particle arrays of buffer `cur` to / from a flat device block
+void state_io(sph_ctx* c, char* blk, bool save, cudaStream_t st, uint32_t n) {
+    Buffers& b = c->b;
+    const int k = c->cur;
+    size_t off = 0;
+    auto mv = [&](void* arr, size_t bytes) {
+        if (save)
+            cudaMemcpyAsync(blk + off, arr, bytes, cudaMemcpyDeviceToDevice, st);
+        else
+            cudaMemcpyAsync(arr, blk + off, bytes, cudaMemcpyDeviceToDevice, st);
+        off += align_up(bytes, 256);
+    };
+    mv(b.pos[k], sizeof(float4) * n);
+    mv(b.vel[k], sizeof(float4) * n);
+    mv(b.phat[k], sizeof(float) * n);
+    mv(b.cell[k], sizeof(uint32_t) * n);
+    mv(b.pinfo[k], sizeof(uint32_t) * n);
+    mv(b.pid[k], sizeof(uint32_t) * n);
+}
+
+size_t state_bytes(uint32_t n) {
+    return 2 * align_up(sizeof(float4) * n, 256) + 4 * align_up(sizeof(uint32_t) * n, 256);
+}
+
+// sorted state + predicted state + cell tables of one step
+void step_io(sph_ctx* c, char* blk, bool save, cudaStream_t st, uint32_t n) {
+    state_io(c, blk, save, st, n);
+    size_t off = state_bytes(n);
+    Buffers& b = c->b;
+    auto mv = [&](void* arr, size_t bytes) {
+        if (save)
+            cudaMemcpyAsync(blk + off, arr, bytes, cudaMemcpyDeviceToDevice, st);
+        else
+            cudaMemcpyAsync(arr, blk + off, bytes, cudaMemcpyDeviceToDevice, st);
+        off += align_up(bytes, 256);
+    };
+    mv(b.pos_s, sizeof(float4) * n);
+    mv(b.vel_s, sizeof(float4) * n);
+    mv(b.phat_s, sizeof(float) * n);
+    mv(b.start, sizeof(uint32_t) * (c->g.n_cells + 2));
+    mv(b.cell_nfluid, sizeof(uint32_t) * (c->g.n_cells + 1));
+}
+
+size_t step_bytes(uint32_t n, uint32_t n_cells) {
+    return state_bytes(n) + 2 * align_up(sizeof(float4) * n, 256) + align_up(sizeof(float) * n, 256) +
+           align_up(sizeof(uint32_t) * (n_cells + 2), 256) + align_up(sizeof(uint32_t) * (n_cells + 1), 256);
+}
+
+// one forward step with the frozen dt; optionally tape the sorted and predicted states
+void rec_step(sph_ctx* c, const Phys& ph, char* tape_blk, int advance, cudaStream_t st) {
+    launch_dt(c->b, c->g, ph, advance, st);
+    enqueue_sort(c, st);
+    launch_build(c->b, c->cur, c->g, ph, st);
+    launch_forces(c->b, c->cur, c->g, ph, kPredict, 0, st);
+    if (tape_blk) step_io(c, tape_blk, true, st, c->tape.n);
+    launch_forces(c->b, c->cur, c->g, ph, kCorrect, 0, st);
+}
+
+}  // namespace
+
+int sph_set_alpha(sph_ctx* c, double alpha) {
+    if (!c || !(alpha >= 0.0) || c->p.visc_model != SPH_VISC_ARTIFICIAL) return SPH_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    c->p.alpha = alpha;
+    for (auto& s : c->scenes_h) s.pi_coef = (float)(alpha * s.pi_unit);
+    CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->scenes_h.size(), cudaMemcpyHostToDevice));
+    drop_graphs(c);
+    c->tape.valid = false;
+    return SPH_OK;
+}
+
+int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out) {
+    if (!c || T == 0 || K == 0 || T % K != 0) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (c->g.n_scenes != 1) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    free_tape(c);
+    AdjTape& t = c->tape;
+    DevStatus hs;
+    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t n = hs.n_active;
+    // frozen dt: the parameter if given, else the CFL dt of one forces call on the initial state (C7)
+    double dt = c->p.dt_fixed;
+    if (!(dt > 0.0)) {
+        launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+        launch_dt(c->b, c->g, c->ph, 0, st);
+        SceneDyn d0;
+        CK(cudaMemcpyAsync(&d0, c->b.dyn, sizeof(d0), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        dt = d0.dt_d;
+    }
+    t.T = T;
+    t.K = K;
+    t.n = n;
+    t.dt = dt;
+    t.ph_rec = c->ph;
+    t.ph_rec.dt_fixed = dt;
+    t.ckpt_bytes = state_bytes(n);
+    t.step_bytes = step_bytes(n, c->g.n_cells);
+    for (uint32_t s2 = 0; s2 < T / K; ++s2) {
+        char* p = nullptr;
+        if (cudaMalloc(&p, t.ckpt_bytes) != cudaSuccess) {
+            free_tape(c);
+            return SPH_ERR_CUDA;
+        }
+        t.ckpt.push_back(p);
+    }
+    const size_t nv = align_up(sizeof(float4) * (size_t)c->g.cap, 256);
+    const size_t nf = align_up(sizeof(float) * (size_t)c->g.cap, 256);
+    if (cudaMalloc((void**)&t.steps, t.step_bytes * K) != cudaSuccess ||
+        cudaMalloc(&t.adj_mem, 7 * nv + 2 * nf + 256) != cudaSuccess) {
+        cudaGetLastError();
+        free_tape(c);
+        return SPH_ERR_CUDA;
+    }
+    char* m = (char*)t.adj_mem;
+    t.a.xb = (float4*)m; m += nv;
+    t.a.ub = (float4*)m; m += nv;
+    t.a.xbs = (float4*)m; m += nv;
+    t.a.ubs = (float4*)m; m += nv;
+    t.a.seed = (float4*)m; m += nv;
+    t.a.xb_id = (float4*)m; m += nv;
+    t.a.ub_id = (float4*)m; m += nv;
+    t.a.dphat = (float*)m; m += nf;
+    t.a.dphat_s = (float*)m; m += nf;
+    t.a.alpha_sum = (double*)m;
+    for (uint32_t s2 = 0; s2 < T; ++s2) {
+        if (s2 % K == 0) state_io(c, t.ckpt[s2 / K], true, st, n);
+        rec_step(c, t.ph_rec, nullptr, 1, st);
+    }
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (hs.n_active != n || hs.error_bits) {
+        free_tape(c);
+        return hs.error_bits ? error_from_bits(hs.error_bits) : SPH_ERR_STATE;
+    }
+    // cell tables and list of the final state for later calls
+    enqueue_build(c, st);
+    CK(cudaStreamSynchronize(st));
+    t.valid = true;
+    c->need_dt0 = true;
+    if (dt_out) *dt_out = dt;
+    return SPH_OK;
+}
+
+int sph_backward(sph_ctx* c, const float* xbar_T, const float* ubar_T, const float* dbar_T, float* xbar_0,
+                 float* ubar_0, float* dbar_0, double* alphabar, void* stream) {
+    if (!c) return SPH_ERR_ARG;
+    AdjTape& t = c->tape;
+    if (!t.valid || !c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    const uint32_t n = t.n;
+    launch_adj_load(t.a, n, xbar_T, ubar_T, dbar_T, st);
+    for (int seg = (int)(t.T / t.K) - 1; seg >= 0; --seg) {
+        // recompute the segment forward from its checkpoint, taping every step
+        state_io(c, t.ckpt[seg], false, st, n);
+        for (uint32_t k = 0; k < t.K; ++k) rec_step(c, t.ph_rec, t.steps + (size_t)k * t.step_bytes, 0, st);
+        // reverse through the segment
+        for (int k = (int)t.K - 1; k >= 0; --k) {
+            step_io(c, t.steps + (size_t)k * t.step_bytes, false, st, n);
+            launch_build(c->b, c->cur, c->g, t.ph_rec, st);
+            launch_adj_dphat(t.a, c->b, c->cur, c->g, t.ph_rec, st);
+            launch_adj_gather(t.a, c->b, c->cur, c->g, st);
+            launch_adj_step(t.a, c->b, c->cur, c->g, t.ph_rec, (float)t.dt, st);
+            launch_adj_scatter(t.a, c->b, c->cur, c->g, st);
+        }
+    }
+    launch_adj_store(t.a, n, xbar_0, ubar_0, dbar_0, st);
+    launch_adj_sum_alpha(t.a, n, t.a.alpha_sum, st);
+    double ab = 0.0;
+    CK(cudaMemcpyAsync(&ab, t.a.alpha_sum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // leave the context at the recorded initial state, with its cell tables and list
+    state_io(c, t.ckpt[0], false, st, n);
+    enqueue_build(c, st);
+    c->need_dt0 = true;
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(st));
+    if (alphabar) *alphabar = ab;
+    DevStatus hs;
+    CK(cudaMemcpy(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost));
+    return error_from_bits(hs.error_bits);
+}
 
 int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_ms) {
     if (!c || !phase_ms) return SPH_ERR_ARG;
@@ -857,6 +1072,7 @@ void sph_destroy(sph_ctx* c) {
     if (!c) return;
     cudaDeviceSynchronize();
     drop_graphs(c);
+    free_tape(c);
     free_cells(c);
     Buffers& b = c->b;
     for (int k = 0; k < 2; ++k) {

@@ -41,6 +41,7 @@ struct SceneDev {
     float c0;
     float phat_coef;         // B / rho0^2: P/rho^2 = phat_coef * delta*poly(delta)/(1+delta)^2
     float pi_coef;           // alpha*h*c0/rho0: Pi = -pi_coef * (u.x)/((r^2+0.01h^2)(1+(d_i+d_j)/2))
+    float pi_unit;           // h*c0/rho0 (d pi_coef / d alpha)
     double dt_cap;           // cfl * min(h/c0, h^2/nu)
 };
 
@@ -80,6 +81,7 @@ struct Phys {
     uint32_t max_neibs;
     uint32_t stride;         // neighbour-major stride (>= cap, multiple of 32)
     uint32_t n_scenes;
+    int gamma_i;             // EOS exponent (integer)
     int build_variant;       // neighbour-build kernel variant (autotuned), see build_variant_name
     int forces_block;        // threads per block of the force kernels (autotuned)
 };
@@ -156,6 +158,30 @@ void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t s
 void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
 void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 uint32_t scan_blocks(uint32_t n_buckets);
+
+// adjoint.cu
+struct AdjBuffers {
+    float* dphat;            // d(P/rho^2)/d delta at n and at the predicted state
+    float* dphat_s;
+    float4* xb;              // (xbar, deltabar) of state n, sorted order of the step
+    float4* ub;              // (ubar, alphabar partial)
+    float4* xbs;             // the same at the predicted state
+    float4* ubs;
+    float4* seed;            // (abar, drhobar) seeds of a VJP
+    float4* xb_id;           // adjoints between steps, indexed by upload id
+    float4* ub_id;
+    double* alpha_sum;
+};
+void launch_adj_dphat(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph,
+                      cudaStream_t st);
+void launch_adj_gather(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_adj_scatter(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_adj_step(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph, float dt,
+                     cudaStream_t st);
+void launch_adj_sum_alpha(const AdjBuffers& a, uint32_t n, double* out, cudaStream_t st);
+void launch_adj_load(const AdjBuffers& a, uint32_t n, const float* xbar, const float* ubar, const float* dbar,
+                     cudaStream_t st);
+void launch_adj_store(const AdjBuffers& a, uint32_t n, float* xbar, float* ubar, float* dbar, cudaStream_t st);
 
 // forces.cu
 enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };

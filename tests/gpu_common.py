@@ -88,3 +88,20 @@ def rel_check(gpu, ref, tol, what, mag=None, c_round=4.0):
         raise AssertionError(f"{what}: {int(bad.sum())}/{bad.size} outside the bound; worst i={k} "
                              f"gpu={gpu[k]} ref={ref[k]} rel={rel[k]:.3e} bound={bound[k] / scale[k]:.3e}")
     return (float(np.max(rel)) if rel.size else 0.0), (float(np.mean(rel <= tol)) if rel.size else 1.0)
+
+
+def oracle_jvp_task(args):
+    """One oracle directional derivative (for a spawn pool): returns (L, dL)."""
+    import oracle as _o
+    pkw, pos, vel, delta, mass, ptype, T, dt, tgt, du, dalpha = args
+    p = _o.params(None, **pkw)
+    return _o.loss_jvp(p, pos, vel, delta, mass, ptype, T, dt, tgt, du, dalpha)
+
+
+def oracle_params_kw(scene, **kw):
+    d = dict(dp=scene.dp, h=scene.h, kernel_radius=scene.kernel_radius, rho0=scene.rho0, c0=scene.c0,
+             gamma=float(scene.gamma), visc_model=scene.visc, alpha=scene.alpha, nu=scene.nu, g=scene.g,
+             cfl=scene.cfl, dt_fixed=scene.dt_fixed, origin=scene.origin, size=scene.size,
+             periodic_mask=scene.periodic)
+    d.update(kw)
+    return d
