@@ -349,13 +349,107 @@ def run_ours(args, world, rank, local):
     sim.close()
 
 
+def run_batch(args):
+    """256 sloshing tanks: one context stepped by one captured graph per step,
+    against one context per tank stepped scene by scene (per-scene launches)."""
+    import torch
+    from paper_2207_11328_gb300 import Simulation, _build, scenes
+    _build.build()
+    b = scenes.sloshing_batch()
+    stream = torch.cuda.current_stream()
+    sim = Simulation.from_scene(b, stream=stream)
+    tuned = sim.autotune(stream=stream)
+    sim.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    st0 = sim.stats(stream=stream)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(0) as clk:
+        ev0.record(stream)
+        sim.step(args.steps, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    t_b = ev0.elapsed_time(ev1) / 1e3
+    st1 = sim.stats(stream=stream)
+    inter_b = 2.0 * (st1["list_entries"] - st0["list_entries"])
+    # per-scene contexts, each tank launched on its own
+    per = []
+    for k, d in enumerate(b.scenes):
+        m = b.scene == k
+        one = scenes.subset(b, m)
+        import dataclasses
+        one = dataclasses.replace(one, scenes=None, scene=np.zeros(int(m.sum()), np.uint32), origin=d["origin"],
+                                  size=d["size"], periodic=d["periodic"], c0=d["c0"])
+        ps = Simulation.from_scene(one, stream=stream)
+        ps.step(args.warmup, stream=stream)
+        per.append(ps)
+    torch.cuda.synchronize()
+    e0 = sum(ps.stats(stream=stream)["list_entries"] for ps in per)
+    ps_steps = max(1, args.steps // 5)
+    ev0.record(stream)
+    for _ in range(ps_steps):
+        for ps in per:
+            ps.step(1, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_p = ev0.elapsed_time(ev1) / 1e3
+    inter_p = 2.0 * (sum(ps.stats(stream=stream)["list_entries"] for ps in per) - e0)
+    line = {"metric": METRIC, "value": inter_b / t_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"sloshing_batch: {len(b.scenes)} tanks, {b.n} particles "
+                                   f"({b.n_fluid} fluid), dp 0.01 m", "autotuned": {"build": tuned[0],
+                                                                                  "forces_block": tuned[1]}},
+            "particle_steps_per_s": b.n * args.steps / t_b,
+            "per_scene_launches": {"value": inter_p / t_p, "ms_per_step": 1e3 * t_p / ps_steps,
+                                   "particle_steps_per_s": b.n * ps_steps / t_p, "steps": ps_steps},
+            "batched_speedup": (inter_b / t_b) / (inter_p / t_p), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
+def run_adjoint(args):
+    """Differentiable run: 32^3 periodic box, T = 64 steps, checkpoint every 8:
+    forward record, backward, and a plain 64-step forward for comparison."""
+    import torch
+    from paper_2207_11328_gb300 import Simulation, _build, scenes
+    _build.build()
+    s = scenes.periodic_box(n_per_axis=32)
+    s.dt_fixed = 3.9e-4
+    stream = torch.cuda.current_stream()
+    sim = Simulation.from_scene(s, stream=stream)
+    sim.autotune(stream=stream)
+    xbar = torch.randn((s.n, 3), device="cuda", dtype=torch.float32)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    times = []
+    for rep in range(args.warmup + 3):
+        sim.upload(s, stream=stream)
+        torch.cuda.synchronize()
+        ev[0].record(stream)
+        sim.record(64, 8, stream=stream)
+        ev[1].record(stream)
+        sim.backward(xbar_T=xbar, stream=stream)
+        ev[2].record(stream)
+        sim.upload(s, stream=stream)
+        sim.step(64, stream=stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    t = np.median(np.array(times), axis=0)
+    line = {"metric": "forward+backward time, 32^3 periodic box, T=64, checkpoint every 8", "value": t[0] + t[1],
+            "unit": "ms", "higher_is_better": False, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "periodic_box_32768, T=64, K=8, dt frozen 3.9e-4 s"},
+            "record_ms": t[0], "backward_ms": t[1], "plain_forward_64_steps_ms_incl_upload": t[2],
+            "backward_over_forward": t[1] / t[0]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box"])
+    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box", "batch", "adjoint"])
     ap.add_argument("--max-neibs", type=int, default=128)
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -369,6 +463,12 @@ def main():
         run_reference(args, int(os.environ.get("WORLD_SIZE", "1")), rank)
         return
     world, rank, local = dist_setup(args.gpus)
+    if args.workload == "batch":
+        run_batch(args)
+        return
+    if args.workload == "adjoint":
+        run_adjoint(args)
+        return
     run_ours(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist

@@ -468,22 +468,32 @@ __global__ void __launch_bounds__(kBlockT) k_build_tpp(
                     const uint32_t e = fluid_i ? start[cc + 1] : ef;
                     const float bx = pi.x - (float)dx * sc.cell_f[0];
                     const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
-                    for (uint32_t j = b; j < e; ++j) {
-                        const float4 pj = pos[j];
-                        const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
-                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        if (r2 < R2 && r2 > 0.f) {
-                            ++nfound;
-                            if (nfw + nbw < max_neibs) {
-                                const uint32_t entry = (j << kCodeBits) | code;
-                                if (j < ef) {
-                                    *pf = entry;
-                                    pf += stride;
-                                    ++nfw;
-                                } else {
-                                    *pb = entry;
-                                    pb -= stride;
-                                    ++nbw;
+                    // four candidates per iteration: independent loads in flight
+                    uint32_t j = b;
+                    for (; j < e; j += 4) {
+                        float r2v[4];
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const uint32_t jj = min(j + u, e - 1);
+                            const float4 pj = pos[jj];
+                            const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                            r2v[u] = j + u < e ? fmaf(rx, rx, fmaf(ry, ry, rz * rz)) : R2;
+                        }
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            if (r2v[u] < R2 && r2v[u] > 0.f) {
+                                ++nfound;
+                                if (nfw + nbw < max_neibs) {
+                                    const uint32_t entry = ((j + u) << kCodeBits) | code;
+                                    if (j + u < ef) {
+                                        *pf = entry;
+                                        pf += stride;
+                                        ++nfw;
+                                    } else {
+                                        *pb = entry;
+                                        pb -= stride;
+                                        ++nbw;
+                                    }
                                 }
                             }
                         }
