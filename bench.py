@@ -142,24 +142,32 @@ def barrier(world):
         dist.barrier()
 
 
-def allmax(world, v):
+def _reduce(world, v, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def allmax(world, v):
+    import torch.distributed as dist
+    return _reduce(world, v, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def allsum(world, v):
-    if world == 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(world, v, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def aggregate(world, interactions_local, particle_steps_local, seconds_local):
+    """Whole-job throughput of independent replicas: work summed over ranks
+    divided by the slowest rank's time (max over ranks)."""
+    t_max = allmax(world, seconds_local)
+    return allsum(world, interactions_local) / t_max, allsum(world, particle_steps_local) / t_max, t_max
 
 
 # ---------------------------------------------------------------------------
@@ -278,9 +286,7 @@ def run_ours(args, world, rank, local):
     entries = st1["list_entries"] - st0["list_entries"]
     inter_local = 2.0 * entries
     psteps_local = float(st1["n_active"]) * args.steps
-    t_max = allmax(world, ms) / 1e3
-    value = allsum(world, inter_local) / t_max
-    psteps = allsum(world, psteps_local) / t_max
+    value, psteps, t_max = aggregate(world, inter_local, psteps_local, ms / 1e3)
     kernels = st1["kernels_per_step"]
 
     # per-kernel durations (same work, launched one by one with events on the launch stream)

@@ -19,6 +19,7 @@ tank, Poiseuille closed form, convergence order, finite differences).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -54,40 +55,58 @@ class Params(ctypes.Structure):
                 ("periodic_mask", ctypes.c_uint32), ("pad1", ctypes.c_uint32)]
 
 
+def _configure(lib):
+    P = ctypes.POINTER(Params)
+    dp_ = ctypes.POINTER(ctypes.c_double)
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    u8p = ctypes.POINTER(ctypes.c_uint8)
+    lib.ora_kernel_W.restype = ctypes.c_double
+    lib.ora_kernel_W.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.ora_kernel_F.restype = ctypes.c_double
+    lib.ora_kernel_F.argtypes = [ctypes.c_double, ctypes.c_double]
+    lib.ora_eos.restype = ctypes.c_double
+    lib.ora_eos.argtypes = [P, ctypes.c_double]
+    lib.ora_neighbors.restype = ctypes.c_int64
+    lib.ora_neighbors.argtypes = [P, ctypes.c_int, dp_, ctypes.c_int, ctypes.c_int64, i64p, i32p]
+    lib.ora_rhs.restype = ctypes.c_int
+    lib.ora_rhs.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, dp_, dp_, dp_]
+    lib.ora_rhs_sample.restype = ctypes.c_int
+    lib.ora_rhs_sample.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int,
+                                   i32p, dp_, dp_, i32p, dp_]
+    lib.ora_cfl_dt.restype = ctypes.c_double
+    lib.ora_cfl_dt.argtypes = [P, ctypes.c_int, dp_, u8p]
+    lib.ora_step.restype = ctypes.c_int
+    lib.ora_step.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int, dp_, dp_]
+    lib.ora_energy.restype = ctypes.c_double
+    lib.ora_energy.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p]
+    lib.ora_loss_jvp.restype = ctypes.c_int
+    lib.ora_loss_jvp.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int,
+                                 ctypes.c_double, dp_, dp_, ctypes.c_double, dp_, dp_]
+    return lib
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            P = ctypes.POINTER(Params)
-            dp_ = ctypes.POINTER(ctypes.c_double)
-            i64p = ctypes.POINTER(ctypes.c_int64)
-            i32p = ctypes.POINTER(ctypes.c_int32)
-            u8p = ctypes.POINTER(ctypes.c_uint8)
-            lib.ora_kernel_W.restype = ctypes.c_double
-            lib.ora_kernel_W.argtypes = [ctypes.c_double, ctypes.c_double]
-            lib.ora_kernel_F.restype = ctypes.c_double
-            lib.ora_kernel_F.argtypes = [ctypes.c_double, ctypes.c_double]
-            lib.ora_eos.restype = ctypes.c_double
-            lib.ora_eos.argtypes = [P, ctypes.c_double]
-            lib.ora_neighbors.restype = ctypes.c_int64
-            lib.ora_neighbors.argtypes = [P, ctypes.c_int, dp_, ctypes.c_int, ctypes.c_int64, i64p, i32p]
-            lib.ora_rhs.restype = ctypes.c_int
-            lib.ora_rhs.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, dp_, dp_, dp_]
-            lib.ora_rhs_sample.restype = ctypes.c_int
-            lib.ora_rhs_sample.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int,
-                                           i32p, dp_, dp_, i32p, dp_]
-            lib.ora_cfl_dt.restype = ctypes.c_double
-            lib.ora_cfl_dt.argtypes = [P, ctypes.c_int, dp_, u8p]
-            lib.ora_step.restype = ctypes.c_int
-            lib.ora_step.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int, dp_, dp_]
-            lib.ora_energy.restype = ctypes.c_double
-            lib.ora_energy.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p]
-            lib.ora_loss_jvp.restype = ctypes.c_int
-            lib.ora_loss_jvp.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, ctypes.c_int,
-                                         ctypes.c_double, dp_, dp_, ctypes.c_double, dp_, dp_]
-            _lib = lib
+            _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+@contextlib.contextmanager
+def using(lib_path):
+    """Run the wrapper against another build of the oracle (used by the tests
+    that plant mistakes in copies of the oracle to show the pins catch them)."""
+    global _lib
+    with _lock:
+        saved = _lib
+        _lib = _configure(ctypes.CDLL(lib_path))
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
 
 
 def _d(a):

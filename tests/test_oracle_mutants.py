@@ -1,0 +1,107 @@
+"""The pins catch plausible mistakes in the oracle.
+
+Each case plants one mistake in a copy of oracle/sph_oracle.cpp (a flipped
+sign, a dropped factor, a wrong coefficient or index, transposed operands, a
+wrong branch), builds it on the CPU and runs the fast pins against it: at
+least one pin must fail.  The oracle itself is never modified."""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from paper_2207_11328_gb300 import scenes
+from tests import test_oracle_integration as ti
+from tests import test_oracle_kernel_eos as tk
+from tests import test_oracle_neighbors as tn
+from tests import test_oracle_physics as tp
+
+MUTANTS = [
+    ("continuity sign", "drho += T(m[j]) * udotx * F;", "drho -= T(m[j]) * udotx * F;"),
+    ("pressure term without m_j", "T coef = T(m[j]) * bracket * F;", "T coef = bracket * F;"),
+    ("pressure sign", "for (int c = 0; c < 3; ++c) a[c] -= coef * d[c];",
+     "for (int c = 0; c < 3; ++c) a[c] += coef * d[c];"),
+    ("gradient coefficient", "return T(105.0 / (128.0 * kPi", "return T(105.0 / (64.0 * kPi"),
+    ("kernel coefficient", "return T(21.0 / (16.0 * kPi", "return T(21.0 / (8.0 * kPi"),
+    ("kernel shape", "* t * t * t * t * (q * 2.0 + T(1.0));", "* t * t * t * (q * 2.0 + T(1.0));"),
+    ("EOS binomial index", "binom = binom * (double)(gam - k + 1) / (double)k;",
+     "binom = binom * (double)(gam - k) / (double)k;"),
+    ("EOS constant B", "double B = P.rho0 * P.c0 * P.c0 / P.gamma;", "double B = P.rho0 * P.c0 / P.gamma;"),
+    ("laminar coefficient", "T lam = T(4.0 * P.nu * m[j])", "T lam = T(2.0 * P.nu * m[j])"),
+    ("laminar sign", "for (int c = 0; c < 3; ++c) a[c] += lam * uij[c];",
+     "for (int c = 0; c < 3; ++c) a[c] -= lam * uij[c];"),
+    ("viscosity switch", "if (P.visc_model == 0 && pv(udotx) < 0.0) {", "if (P.visc_model == 0 && pv(udotx) > 0.0) {"),
+    ("viscosity density mean", "T rhobar = (rho[i] + rho[j]) * 0.5;", "T rhobar = (rho[i] + rho[j]);"),
+    ("transposed separation", "d[a] = xi[a] - xj[a];", "d[a] = xj[a] - xi[a];"),
+    ("minimum image", "double k = std::nearbyint(pv(d[a]) / L);", "double k = std::floor(pv(d[a]) / L);"),
+    ("bins smaller than the radius", "int k = (int)std::floor(P.size[a] / R);",
+     "int k = (int)std::floor(P.size[a] / R) + 1;"),
+    ("gravity on boundary particles", "for (int c = 0; c < 3; ++c) a_out[c] = T(0.0);",
+     "for (int c = 0; c < 3; ++c) a_out[c] = T(P.g[c]);"),
+    ("boundary velocity used", "uij[c] = ui[c] - (fluid_j ? u[3 * j + c] : T(0.0));", "uij[c] = ui[c] - u[3 * j + c];"),
+    ("predictor full step", "us[3 * i + c] = u[3 * i + c] + T(0.5 * dt) * a[3 * i + c];",
+     "us[3 * i + c] = u[3 * i + c] + T(dt) * a[3 * i + c];"),
+    ("corrector forward Euler position", "x[3 * i + c] = x[3 * i + c] + T(0.5 * dt) * (u[3 * i + c] + un);",
+     "x[3 * i + c] = x[3 * i + c] + T(dt) * un;"),
+    ("density integrated without 1/rho0", "delta[i] = delta[i] + T(dt / rho0) * drho[i];",
+     "delta[i] = delta[i] + T(dt) * drho[i];"),
+    ("CFL acceleration branch", "dt = std::min(dt, std::sqrt(P.h / std::sqrt(amax2)));",
+     "dt = std::min(dt, P.h / std::sqrt(amax2));"),
+    ("dual sqrt derivative", "return Dual(s, a.d / (2.0 * s));", "return Dual(s, a.d / s);"),
+    ("dual product rule", "return Dual(a.v * b.v, a.d * b.v + a.v * b.d);", "return Dual(a.v * b.v, a.d * b.v);"),
+]
+
+
+def _box8():
+    s = scenes.periodic_box(n_per_axis=8, dp=0.02)
+    return s, s.pos + scenes.seeded_normal(s.pos.shape, 0.1 * 0.02, 7)
+
+
+# fast pins first; each returns normally or raises AssertionError
+BATTERY = [
+    tk.test_unit_integral, tk.test_F_moment_closed_form, tk.test_shape_matches_listing, tk.test_F_is_dW_dr_over_r,
+    lambda: tk.test_eos_binomial_exact(0.01), tk.test_eos_sound_speed,
+    lambda: tn.test_brute_matches_numpy(7), lambda: tn.test_grid_matches_brute(7), tn.test_lattice_interior_count_is_80,
+    tp.test_continuity_linear_field, tp.test_continuity_sign_approaching_pair, tp.test_pressure_gradient_linear_density,
+    tp.test_mass_factor_in_pressure_term, tp.test_artificial_viscosity_switch, tp.test_laminar_shear_closed_form,
+    tp.test_boundary_particles, tp.test_cfl_dt_branches, tp.test_artificial_viscosity_shear_decay,
+    lambda: tp.test_momentum_conserved_periodic(1, 0.0, 0.1),
+    lambda: ti.test_jvp_matches_central_differences_smooth(_box8()),
+    ti.test_first_dt_from_initial_forces_and_cfl, ti.test_energy_non_increasing_with_artificial_viscosity,
+    ti.test_predictor_corrector_second_order,
+]
+
+
+@pytest.fixture(scope="module")
+def source():
+    with open(oracle._SRC) as f:
+        return f.read()
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(name, old, new, source, tmp_path):
+    assert source.count(old) >= 1, f"mutation site not found: {name}"
+    src = tmp_path / "mutant.cpp"
+    src.write_text(source.replace(old, new, 1))
+    lib = tmp_path / "libmutant.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           str(src), "-o", str(lib)])
+    with oracle.using(str(lib)):
+        for pin in BATTERY:
+            try:
+                pin()
+            except (AssertionError, RuntimeError):
+                return
+    pytest.fail(f"planted mistake '{name}' passed every pin")
+
+
+def test_unmutated_copy_passes_the_battery(source, tmp_path):
+    src = tmp_path / "same.cpp"
+    src.write_text(source)
+    lib = tmp_path / "libsame.so"
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           str(src), "-o", str(lib)])
+    with oracle.using(str(lib)):
+        for pin in BATTERY:
+            pin()
+    assert os.path.exists(lib)

@@ -186,3 +186,39 @@ def test_cfl_dt_branches():
     assert oracle.cfl_dt(p, a_big, np.ones(1, np.uint8)) == pytest.approx(0.3 * h / 20.0)
     pl = _params(cfl=0.3, c0=1.0, visc_model=1, nu=0.1)
     assert oracle.cfl_dt(pl, np.zeros((1, 3)), np.zeros(1, np.uint8)) == pytest.approx(0.3 * h * h / 0.1)
+
+
+def test_artificial_viscosity_shear_decay():
+    # C4 magnitude: in the long-wave limit the Monaghan term with the approach
+    # switch acts on a divergence-free shear as nu = alpha h c0 / 20 (the
+    # unswitched term gives (alpha h c0/10)(lap u + 2 grad div u); the switch
+    # keeps half of the fourth moment).  On the lattice the fourth moment is
+    # the quadrature sum below (with the 0.01 h^2 regularisation).  A shear
+    # wave u_x = A sin(k y) must decay at nu k^2 times that quadrature factor.
+    n = 16
+    s = scenes.periodic_box(n_per_axis=n, dp=DP)
+    h = s.h
+    k = 2 * np.pi / (n * DP)
+    lat = 0.0
+    for i in range(-3, 4):
+        for j in range(-3, 4):
+            for l in range(-3, 4):
+                x = np.array([i, j, l]) * DP
+                r2 = x @ x
+                if 0 < r2 < (2 * h) ** 2:
+                    lat += DP ** 3 * x[0] ** 2 * x[1] ** 2 * oracle.kernel_F(np.sqrt(r2), h) / (r2 + 0.01 * h * h)
+    quad = lat / -0.2          # continuum value of the moment: (1/15) int r^2 F dV = -3/15
+    alpha = 0.1
+    u = np.zeros((s.n, 3))
+    u[:, 0] = 1e-3 * np.sin(k * s.pos[:, 1])
+    p = oracle.params(s, alpha=alpha, dt_fixed=3.9e-4)
+    x, v, d = s.pos, u, s.delta.astype(float)
+    ts, amps, t = [], [], 0.0
+    for _ in range(5):
+        x, v, d, _, _ = oracle.step(p, x, v, d, s.mass, s.ptype, 10)
+        t += 10 * 3.9e-4
+        ts.append(t)
+        amps.append(2 * np.mean(v[:, 0] * np.sin(k * x[:, 1])))
+    rate = -np.polyfit(ts, np.log(amps), 1)[0]
+    nu = rate / k ** 2
+    assert nu / (alpha * s.h * s.c0 / 20 * quad) == pytest.approx(1.0, abs=0.03)
