@@ -44,11 +44,13 @@ extern "C" {
 #define SPH_ERR_NONFINITE      -6  /* non-finite value in the uploaded or integrated state */
 #define SPH_ERR_TIMEOUT        -7  /* a bounded device wait gave up */
 #define SPH_ERR_STATE          -8  /* call out of order (e.g. step before upload) */
+#define SPH_ERR_SKIN           -9  /* a particle moved more than skin/2 since the last list build */
 
 /* device error word bits (sph_stats.error_bits) */
 #define SPH_EBIT_NEIB_OVERFLOW  1u
 #define SPH_EBIT_NONFINITE      2u
 #define SPH_EBIT_TIMEOUT        4u
+#define SPH_EBIT_SKIN           8u
 
 /* viscosity models (paper Table 1 "viscous model", Section 2.1) */
 #define SPH_VISC_ARTIFICIAL     0  /* Monaghan artificial viscosity Pi_ij inside the pressure bracket */
@@ -81,6 +83,14 @@ typedef struct {
     uint32_t max_particles;  /* capacity, <= 2^26 */
     uint32_t max_neibs;      /* neighbour-list slots per particle, 8..1024 */
     uint32_t n_scenes;       /* 1, or the number of scenes given to sph_set_scenes */
+    uint32_t rebuild_every;  /* 0 or 1: neighbour pipeline every step.  k > 1: list radius enlarged
+                                by `skin` (paper Section 7: GPUSPH rebuilds every 10 steps with an
+                                enlarged radius); the device runs the pipeline when a particle has
+                                moved skin/4 since the last build, or after k steps, so the list
+                                covers every pair within the influence radius (a displacement past
+                                skin/2 is reported: SPH_ERR_SKIN).  Not with sph_record. */
+    uint32_t pad1;
+    double   skin;           /* added to the list radius when rebuild_every > 1 (>= 0) */
 } sph_params;
 
 /* One independent scene of a batch: its own domain, grid and sound speed. */
@@ -105,6 +115,11 @@ typedef struct {
     uint32_t kernels_per_step;/* kernel launches in one captured step (0 before the first step) */
     uint64_t list_entries;    /* neighbour-list entries written by all builds since upload;
                                  each step's two force passes read its build's entries twice */
+    uint64_t interactions;    /* pairs within the influence radius evaluated by the first force
+                                 pass of each step since upload, counted when rebuild_every > 1 */
+    uint32_t builds;          /* neighbour-list builds run by the upload and the steps since upload
+                                 (one per step when rebuild_every <= 1) */
+    uint32_t pad;
 } sph_stats;
 
 /* Create a context on the current CUDA device and allocate every device
@@ -193,16 +208,18 @@ int sph_backward(sph_ctx* ctx, const float* xbar_T, const float* ubar_T, const f
 
 /* Autotuner (launch shapes only; results are unchanged): times each
  * neighbour-build variant (one thread per particle with 128 or 256 threads
- * per block, or one warp per cell with 2, 4 or 8 cells per block) and the
- * force kernels at 64, 128 and 256 threads per block on the uploaded state
+ * per block, or one warp per cell with 2, 4 or 8 cells per block) and each
+ * force-kernel shape (64, 128 or 256 threads per block; 128 threads with a
+ * register cap for 10 or 12 resident blocks per SM) on the uploaded state
  * (3 timed launches each, CUDA events on `stream`), keeps the fastest and
  * re-captures the step graph on the next sph_step.  Outputs (nullable): the
- * chosen build variant (see sph_build_variant_name) and force block size.
+ * chosen variants (names: sph_build_variant_name, sph_forces_variant_name).
  * Synchronises `stream`; SPH_ERR_STATE before an upload. */
-int sph_autotune(sph_ctx* ctx, void* stream, int* build_variant, int* forces_block);
+int sph_autotune(sph_ctx* ctx, void* stream, int* build_variant, int* forces_variant);
 
-/* Name of a neighbour-build variant of sph_autotune (static storage). */
+/* Names of the variants of sph_autotune (static storage). */
 const char* sph_build_variant_name(int variant);
+const char* sph_forces_variant_name(int variant);
 
 /* Same work as sph_step, launched kernel by kernel (no graph) with CUDA
  * events recorded on `stream` between the launches; adds the elapsed

@@ -24,7 +24,8 @@ LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
 
 SPH_OK = 0
 _ERRNAMES = {-1: "SPH_ERR_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_CAPACITY", -4: "SPH_ERR_NEIB_OVERFLOW",
-             -5: "SPH_ERR_OUT_OF_DOMAIN", -6: "SPH_ERR_NONFINITE", -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE"}
+             -5: "SPH_ERR_OUT_OF_DOMAIN", -6: "SPH_ERR_NONFINITE", -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE",
+             -9: "SPH_ERR_SKIN"}
 
 
 class SphError(RuntimeError):
@@ -41,7 +42,8 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3),
                 ("periodic_mask", ctypes.c_uint32), ("max_particles", ctypes.c_uint32),
-                ("max_neibs", ctypes.c_uint32), ("n_scenes", ctypes.c_uint32)]
+                ("max_neibs", ctypes.c_uint32), ("n_scenes", ctypes.c_uint32),
+                ("rebuild_every", ctypes.c_uint32), ("pad1", ctypes.c_uint32), ("skin", ctypes.c_double)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -54,7 +56,8 @@ class Stats(ctypes.Structure):
                 ("max_neibs_seen", ctypes.c_uint32), ("error_bits", ctypes.c_uint32),
                 ("steps", ctypes.c_uint64), ("dt", ctypes.c_double), ("time", ctypes.c_double),
                 ("n_cells", ctypes.c_uint32), ("kernels_per_step", ctypes.c_uint32),
-                ("list_entries", ctypes.c_uint64)]
+                ("list_entries", ctypes.c_uint64), ("interactions", ctypes.c_uint64),
+                ("builds", ctypes.c_uint32), ("pad0", ctypes.c_uint32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
@@ -87,6 +90,7 @@ _SIGS = {
     "sph_record": [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp],
     "sph_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
     "sph_build_variant_name": [ctypes.c_int],
+    "sph_forces_variant_name": [ctypes.c_int],
     "sph_strerror": [ctypes.c_int],
     "sph_destroy": [_vp],
 }
@@ -109,6 +113,7 @@ def _lib():
             fn.restype = ctypes.c_int
         lib.sph_strerror.restype = ctypes.c_char_p
         lib.sph_build_variant_name.restype = ctypes.c_char_p
+        lib.sph_forces_variant_name.restype = ctypes.c_char_p
         lib.sph_destroy.restype = None
         _LIB = lib
     return _LIB
@@ -132,7 +137,7 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def params_from_scene(scene, max_particles=None, max_neibs=128):
+def params_from_scene(scene, max_particles=None, max_neibs=128, rebuild_every=1, skin=0.0):
     p = Params()
     p.dp, p.h, p.kernel_radius = scene.dp, scene.h, scene.kernel_radius
     p.rho0, p.c0, p.gamma = scene.rho0, scene.c0, float(scene.gamma)
@@ -145,6 +150,8 @@ def params_from_scene(scene, max_particles=None, max_neibs=128):
     p.max_particles = int(max_particles or max(scene.n, 1))
     p.max_neibs = int(max_neibs)
     p.n_scenes = 1
+    p.rebuild_every = int(rebuild_every)
+    p.skin = float(skin)
     return p
 
 
@@ -169,8 +176,9 @@ class Simulation:
         self.n_scenes = len(scenes_desc) if scenes_desc else 1
 
     @classmethod
-    def from_scene(cls, scene, max_particles=None, max_neibs=128, upload=True, stream=None):
-        sim = cls(params_from_scene(scene, max_particles, max_neibs), scene.scenes)
+    def from_scene(cls, scene, max_particles=None, max_neibs=128, upload=True, stream=None, rebuild_every=1,
+                   skin=0.0):
+        sim = cls(params_from_scene(scene, max_particles, max_neibs, rebuild_every, skin), scene.scenes)
         if upload:
             sim.upload(scene, stream=stream)
         return sim
@@ -273,13 +281,13 @@ class Simulation:
         _check(_lib().sph_step(self._h, int(nsteps), _stream_handle(stream)), "sph_step")
 
     def autotune(self, stream=None):
-        """Pick the fastest neighbour-build variant and force block size on the
-        uploaded state; returns (build variant name, force threads per block)."""
+        """Pick the fastest neighbour-build variant and force-kernel launch shape
+        on the uploaded state; returns (build variant name, forces variant name)."""
         v = ctypes.c_int()
-        fb = ctypes.c_int()
-        _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fb)),
+        fv = ctypes.c_int()
+        _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fv)),
                "sph_autotune")
-        return _lib().sph_build_variant_name(v.value).decode(), fb.value
+        return _lib().sph_build_variant_name(v.value).decode(), _lib().sph_forces_variant_name(fv.value).decode()
 
     # ---- differentiable run ---------------------------------------------------
     def set_alpha(self, alpha):

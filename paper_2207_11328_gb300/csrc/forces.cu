@@ -25,34 +25,49 @@ namespace sphg {
 
 namespace {
 
-__device__ __forceinline__ float cell_delta(uint32_t bits2, float cell) {
-    // bits2 = d + 1 in {0, 1, 2}  ->  d * cell
-    return bits2 == 0u ? -cell : (bits2 == 2u ? cell : 0.0f);
-}
-
 struct Acc {
     float ax, ay, az, drho;
 };
 
+// The central particle's offset seen from a neighbour cell: o_i - d*cell for
+// d = -1, 0, +1 per axis (list entries carry d + 1 in two bits per axis).
+struct Central {
+    float xm, x0, xp, ym, y0, yp, zm, z0, zp;
+};
+
+__device__ __forceinline__ Central central_of(const float4& pi, float cx, float cy, float cz) {
+    return Central{pi.x + cx, pi.x, pi.x - cx, pi.y + cy, pi.y, pi.y - cy, pi.z + cz, pi.z, pi.z - cz};
+}
+
+__device__ __forceinline__ float pick(uint32_t b, float m, float z, float p) {
+    return (b & 1u) ? z : ((b & 2u) ? p : m);
+}
+
 // One neighbour of a fluid particle.  BND: the neighbour is a boundary
-// particle (mass stored negated, velocity zero).
-template <int VISC, bool BND>
-__device__ __forceinline__ void fluid_pair(uint32_t e, const float4& pi, const float4& vi, float phat_i,
+// particle (mass stored negated, velocity zero).  The kernel constant aF is
+// factored out of every term (all terms are linear in F) and applied once.
+template <int VISC, bool BND, bool SKIN>
+__device__ __forceinline__ void fluid_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i,
                                            const float4* __restrict__ pos, const float4* __restrict__ vel,
-                                           const float* __restrict__ phat, float cx, float cy, float cz,
-                                           float pi_coef, const Phys& ph, Acc& acc) {
+                                           const float* __restrict__ phat, float pi_coef, const Phys& ph, Acc& acc,
+                                           uint32_t& npairs) {
     const uint32_t j = e >> kCodeBits;
     const float4 pj = pos[j];
-    const float4 vj = vel[j];
+    const float4 vj = vel[j];       // all gathers issued together
     const float phat_j = phat[j];
-    const float rx = pi.x - pj.x - cell_delta(e & 3u, cx);
-    const float ry = pi.y - pj.y - cell_delta((e >> 2) & 3u, cy);
-    const float rz = pi.z - pj.z - cell_delta((e >> 4) & 3u, cz);
+    const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;
+    const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
+    const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
     const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
+    if (SKIN) {
+        // list with a skin: pairs beyond the influence radius (F = 0) skip the arithmetic
+        if (!(r2 < ph.R2)) return;
+        ++npairs;
+    }
     const float r = r2 * rsqrtf(r2);
     const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
     const float mj = BND ? -pj.w : pj.w;
-    const float mF = mj * ph.aF * (t * t * t);
+    const float mF = mj * (t * t * t);  // m_j F / aF
     const float ux = BND ? vi.x : vi.x - vj.x;
     const float uy = BND ? vi.y : vi.y - vj.y;
     const float uz = BND ? vi.z : vi.z - vj.z;
@@ -77,14 +92,17 @@ __device__ __forceinline__ void fluid_pair(uint32_t e, const float4& pi, const f
     }
 }
 
-template <int VISC, int MODE, int kBlock>
-__global__ void __launch_bounds__(kBlock) k_forces(
+// SKIN: the list carries a skin (rebuild every k steps): skip pairs beyond the
+// cutoff, count the pairs within it (first pass), check the displacement (corrector)
+template <int VISC, int MODE, int kBlock, int kMinBlocks, bool SKIN>
+__global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
-    int acc_dt) {
+    int acc_dt, const float4* __restrict__ pos_ref) {
     const uint32_t n = st->n_active;
+    uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint32_t s = pinfo[i];
         const SceneDev& sc = scenes[s];
@@ -98,33 +116,36 @@ __global__ void __launch_bounds__(kBlock) k_forces(
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
+            const Central ci = central_of(pi, cx, cy, cz);
             // list entries come from DRAM: load four slots ahead of their use
             const size_t S = ph.stride;
             const uint32_t* lp = nlist + i;
             uint32_t k = 0;
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
-                fluid_pair<VISC, false>(e0, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-                fluid_pair<VISC, false>(e1, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-                fluid_pair<VISC, false>(e2, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-                fluid_pair<VISC, false>(e3, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, false, SKIN>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, false, SKIN>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, false, SKIN>(e2, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, false, SKIN>(e3, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
             }
             for (; k < nf; ++k, lp += S)
-                fluid_pair<VISC, false>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, false, SKIN>(__ldg(lp), ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             k = 0;
             for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
-                fluid_pair<VISC, true>(e0, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-                fluid_pair<VISC, true>(e1, pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
+                fluid_pair<VISC, true, SKIN>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, true, SKIN>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
             }
             for (; k < nb; ++k, lp -= S)
-                fluid_pair<VISC, true>(__ldg(lp), pi, vi, phat_i, pos, vel, phat, cx, cy, cz, pic, ph, acc);
-            acc.ax += ph.g[0];
-            acc.ay += ph.g[1];
-            acc.az += ph.g[2];
+                fluid_pair<VISC, true, SKIN>(__ldg(lp), ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+            acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
+            acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
+            acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
+            acc.drho *= ph.aF;
         } else {
             // boundary particle: continuity over its fluid neighbours, u_i = 0
+            const Central ci = central_of(pi, cx, cy, cz);
             const uint32_t* lp = nlist + i;
 #pragma unroll 2
             for (uint32_t k = 0; k < nf; ++k, lp += ph.stride) {
@@ -132,16 +153,21 @@ __global__ void __launch_bounds__(kBlock) k_forces(
                 const uint32_t j = e >> kCodeBits;
                 const float4 pj = pos[j];
                 const float4 vj = vel[j];
-                const float rx = pi.x - pj.x - cell_delta(e & 3u, cx);
-                const float ry = pi.y - pj.y - cell_delta((e >> 2) & 3u, cy);
-                const float rz = pi.z - pj.z - cell_delta((e >> 4) & 3u, cz);
+                const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;
+                const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
+                const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
                 const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
+                if (SKIN) {
+                    if (!(r2 < ph.R2)) continue;
+                    ++npairs;
+                }
                 const float r = r2 * rsqrtf(r2);
                 const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
-                const float mF = pj.w * ph.aF * (t * t * t);
+                const float mF = pj.w * (t * t * t);
                 const float udx = -fmaf(vj.x, rx, fmaf(vj.y, ry, vj.z * rz));
                 acc.drho = fmaf(mF, udx, acc.drho);
             }
+            acc.drho *= ph.aF;
         }
 
         if (MODE == kForcesOnly) {
@@ -181,6 +207,18 @@ __global__ void __launch_bounds__(kBlock) k_forces(
                 io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
                 const float chk = po.x + po.y + po.z + vo.x + vo.y + vo.z + vo.w;
                 if (!isfinite(chk)) atomicOr(&st->error_bits, SPH_EBIT_NONFINITE);
+                if (SKIN) {
+                    // the list (built with a skin) covers the cutoff while no particle has
+                    // moved more than skin/2 since the build; the largest displacement
+                    // decides the next rebuild (k_dt)
+                    const float4 r0 = pos_ref[i];
+                    const float dx = po.x - r0.x, dy = po.y - r0.y, dz = po.z - r0.z;
+                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                    if (d2 > ph.skin_lim2) atomicOr(&st->error_bits, SPH_EBIT_SKIN);
+                    const unsigned mk = __activemask();
+                    const uint32_t m = __reduce_max_sync(mk, __float_as_uint(d2));
+                    if ((threadIdx.x & 31) == (uint32_t)(__ffs(mk) - 1)) atomicMax(&st->maxdisp2_bits, m);
+                }
             }
         }
         if (MODE == kCorrect || acc_dt) {
@@ -196,12 +234,17 @@ __global__ void __launch_bounds__(kBlock) k_forces(
             }
         }
     }
+    if (SKIN && MODE == kPredict) {
+        const uint32_t w = __reduce_add_sync(0xffffffffu, npairs);
+        if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->interactions, (unsigned long long)w);
+    }
 }
 
 // One thread per scene: dt for the coming step (reading C7), simulated
 // time, reset of the |a|^2 accumulator.
 __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
-                     uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance) {
+                     uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance, uint32_t rebuild_every,
+                     float trig2) {
     for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
         double dt;
         if (dt_fixed > 0.0) {
@@ -216,39 +259,66 @@ __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__
         if (advance) dyn[s].time += dt;
         dyn[s].amax2_bits = 0u;
     }
-    if (threadIdx.x == 0 && advance) st->steps += 1ull;
+    if (threadIdx.x == 0 && advance) {
+        st->steps += 1ull;
+        if (rebuild_every > 1) {
+            // skin list: rebuild when a particle has moved skin/4 (the predicted state of
+            // the step then stays within skin/2: a CFL step moves less than 0.3 h) or after
+            // rebuild_every steps
+            const bool rb = st->since >= rebuild_every || __uint_as_float(st->maxdisp2_bits) > trig2;
+            st->rebuild = rb ? 1u : 0u;
+            st->since = rb ? 1u : st->since + 1u;
+            if (rb) st->maxdisp2_bits = 0u;
+            st->builds += rb ? 1u : 0u;
+        } else {
+            st->builds += 1u;
+        }
+    }
 }
 
-template <int VISC, int B>
-void launch_forces_b(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
+template <int VISC, int B, int MB, bool SKIN>
+void launch_forces_s(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
                      cudaStream_t st) {
     const unsigned grid = g.cap ? (g.cap + B - 1) / B : 1;
     switch (mode) {
         case kForcesOnly:
-            k_forces<VISC, kForcesOnly, B><<<grid, B, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr,
-                                                                nullptr, b.force, b.pinfo[cur], b.nlist, b.ncount,
-                                                                b.scenes, b.dyn, b.status, ph, acc_dt);
+            k_forces<VISC, kForcesOnly, B, MB, SKIN><<<grid, B, 0, st>>>(
+                b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr, nullptr, b.force, b.pinfo[cur], b.nlist,
+                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, nullptr);
             break;
         case kPredict:
-            k_forces<VISC, kPredict, B><<<grid, B, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s,
-                                                             b.phat_s, nullptr, b.pinfo[cur], b.nlist, b.ncount,
-                                                             b.scenes, b.dyn, b.status, ph, 0);
+            k_forces<VISC, kPredict, B, MB, SKIN><<<grid, B, 0, st>>>(
+                b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s, b.phat_s, nullptr, b.pinfo[cur], b.nlist,
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, nullptr);
             break;
         case kCorrect:
-            k_forces<VISC, kCorrect, B><<<grid, B, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur],
-                                                             b.phat[cur], nullptr, b.pinfo[cur], b.nlist, b.ncount,
-                                                             b.scenes, b.dyn, b.status, ph, 0);
+            k_forces<VISC, kCorrect, B, MB, SKIN><<<grid, B, 0, st>>>(
+                b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur], b.nlist,
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, b.pos_ref);
             break;
     }
 }
 
+template <int VISC, int B, int MB>
+void launch_forces_b(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
+                     cudaStream_t st, bool skin) {
+    if (skin)
+        launch_forces_s<VISC, B, MB, true>(b, cur, g, ph, mode, acc_dt, st);
+    else
+        launch_forces_s<VISC, B, MB, false>(b, cur, g, ph, mode, acc_dt, st);
+}
+
+// launch shapes of the force kernels (autotuned): threads per block and the
+// register cap implied by a minimum of resident blocks per SM
 template <int VISC>
 void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
-                     cudaStream_t st) {
-    switch (ph.forces_block) {
-        case 64: launch_forces_b<VISC, 64>(b, cur, g, ph, mode, acc_dt, st); break;
-        case 256: launch_forces_b<VISC, 256>(b, cur, g, ph, mode, acc_dt, st); break;
-        default: launch_forces_b<VISC, 128>(b, cur, g, ph, mode, acc_dt, st); break;
+                     cudaStream_t st, bool skin) {
+    switch (ph.forces_variant) {
+        case 0: launch_forces_b<VISC, 64, 16>(b, cur, g, ph, mode, acc_dt, st, skin); break;
+        case 2: launch_forces_b<VISC, 256, 4>(b, cur, g, ph, mode, acc_dt, st, skin); break;
+        case 3: launch_forces_b<VISC, 128, 6>(b, cur, g, ph, mode, acc_dt, st, skin); break;
+        case 4: launch_forces_b<VISC, 128, 4>(b, cur, g, ph, mode, acc_dt, st, skin); break;
+        default: launch_forces_b<VISC, 128, 8>(b, cur, g, ph, mode, acc_dt, st, skin); break;
     }
 }
 
@@ -256,14 +326,23 @@ void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& p
 
 void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
                    cudaStream_t st) {
+    const bool skin = b.pos_ref != nullptr;
     if (ph.visc == SPH_VISC_LAMINAR)
-        launch_forces_v<SPH_VISC_LAMINAR>(b, cur, g, ph, mode, acc_dt, st);
+        launch_forces_v<SPH_VISC_LAMINAR>(b, cur, g, ph, mode, acc_dt, st, skin);
     else
-        launch_forces_v<SPH_VISC_ARTIFICIAL>(b, cur, g, ph, mode, acc_dt, st);
+        launch_forces_v<SPH_VISC_ARTIFICIAL>(b, cur, g, ph, mode, acc_dt, st, skin);
+}
+
+const char* forces_variant_name(int v) {
+    static const char* names[kForcesVariants] = {"64 threads, <=64 regs", "128 threads, <=64 regs",
+                                                 "256 threads, <=64 regs", "128 threads, <=85 regs",
+                                                 "128 threads, <=128 regs"};
+    return v >= 0 && v < kForcesVariants ? names[v] : "?";
 }
 
 void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st) {
-    k_dt<<<1, 256, 0, st>>>(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, advance_time);
+    k_dt<<<1, 256, 0, st>>>(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, advance_time,
+                            ph.rebuild_every, ph.skin_trig2);
 }
 
 }  // namespace sphg

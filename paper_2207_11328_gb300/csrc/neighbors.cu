@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(kBlock) k_hash(const float4* __restrict__ pos,
                                                  const SceneDev* __restrict__ scenes,
                                                  const DevStatus* __restrict__ st, uint32_t* __restrict__ key,
                                                  uint32_t* __restrict__ slot, uint32_t* __restrict__ count,
-                                                 uint32_t sentinel) {
+                                                 uint32_t sentinel, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const SceneDev& sc = scenes[pinfo[i]];
@@ -100,7 +101,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* total)
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ count, uint32_t nb,
-                                                              uint32_t* __restrict__ bsum) {
+                                                              uint32_t* __restrict__ bsum,
+                                                              const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
+
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t s = 0;
 #pragma unroll
@@ -111,7 +115,10 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
     if (threadIdx.x == 0) bsum[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* __restrict__ bsum, uint32_t nblocks) {
+__global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* __restrict__ bsum, uint32_t nblocks,
+                                                     const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
+
     uint32_t carry = 0;
     for (uint32_t base = 0; base < nblocks; base += blockDim.x) {
         const uint32_t i = base + threadIdx.x;
@@ -126,7 +133,10 @@ __global__ void __launch_bounds__(1024) k_scan_bsums(uint32_t* __restrict__ bsum
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict__ count, uint32_t nb,
                                                             const uint32_t* __restrict__ bsum,
                                                             uint32_t* __restrict__ start,
-                                                            DevStatus* __restrict__ st) {
+                                                            DevStatus* __restrict__ st,
+                                                            const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
+
     const uint32_t base = blockIdx.x * kScanTile + threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -160,7 +170,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
 // ---------------------------------------------------------------------
 __global__ void __launch_bounds__(kBlock) k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
                                                     const uint32_t* __restrict__ start,
-                                                    const DevStatus* __restrict__ st, uint32_t* __restrict__ unsorted) {
+                                                    const DevStatus* __restrict__ st, uint32_t* __restrict__ unsorted,
+                                                    const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
         unsorted[start[key[i]] + slot[i]] = i;
@@ -183,7 +195,9 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
     const SceneDev* __restrict__ scenes, uint32_t n_cells, DevStatus* __restrict__ st, uint32_t* __restrict__ cell_nfluid,
     float4* __restrict__ pos_o,
     float4* __restrict__ vel_o, float* __restrict__ phat_o, uint32_t* __restrict__ cell_o,
-    uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o) {
+    uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
+
     const int lane = threadIdx.x & 31;
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -255,7 +269,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
     const float4* __restrict__ pos, const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ start,
     const uint32_t* __restrict__ cell_nfluid, const SceneDev* __restrict__ scenes, uint32_t n_cells,
     DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,
-    uint32_t max_neibs, uint32_t stride) {
+    uint32_t max_neibs, uint32_t stride, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
     __shared__ float4 sq[kBuildWarps][kStage];
     __shared__ uint32_t se[kBuildWarps][kStage];
     const int lane = threadIdx.x & 31;
@@ -430,7 +445,8 @@ __global__ void __launch_bounds__(kBlockT) k_build_tpp(
     const float4* __restrict__ pos, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ start, const uint32_t* __restrict__ cell_nfluid, const SceneDev* __restrict__ scenes,
     DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,
-    uint32_t max_neibs, uint32_t stride) {
+    uint32_t max_neibs, uint32_t stride, const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;  // skin list: no rebuild this step
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const SceneDev& sc = scenes[pinfo[i]];
@@ -529,20 +545,20 @@ uint32_t scan_blocks(uint32_t n_buckets) { return (n_buckets + kScanTile - 1) / 
 void launch_hash(const Buffers& b, int cur, const Geometry& g, const Phys& ph, int do_dt, cudaStream_t st) {
     (void)ph; (void)do_dt;
     k_hash<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.pos[cur], b.cell[cur], b.pinfo[cur], b.scenes, b.status,
-                                                        b.key, b.slot, b.count, g.n_cells);
+                                                        b.key, b.slot, b.count, g.n_cells, b.gate);
 }
 
 void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st) {
     const uint32_t nb = g.n_cells + 1;
     const uint32_t blocks = scan_blocks(nb);
-    k_scan_reduce<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum);
-    k_scan_bsums<<<1, 1024, 0, st>>>(b.bsum, blocks);
-    k_scan_down<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum, b.start, b.status);
+    k_scan_reduce<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum, b.gate);
+    k_scan_bsums<<<1, 1024, 0, st>>>(b.bsum, blocks, b.gate);
+    k_scan_down<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum, b.start, b.status, b.gate);
 }
 
 void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
     (void)cur;
-    k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted);
+    k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted, b.gate);
 }
 
 void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
@@ -551,8 +567,9 @@ void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t s
     uint32_t blocks = (g.n_cells + warps_per_block - 1) / warps_per_block;
     if (blocks == 0) blocks = 1;
     k_reorder<<<blocks, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], b.pinfo[cur], b.pid[cur], b.start,
-                                          b.unsorted, b.scenes, g.n_cells, b.status, b.cell_nfluid, b.pos[nxt], b.vel[nxt],
-                                          b.phat[nxt], b.cell[nxt], b.pinfo[nxt], b.pid[nxt]);
+                                          b.unsorted, b.scenes, g.n_cells, b.status, b.cell_nfluid,
+                                          b.pos[nxt], b.vel[nxt],
+                                          b.phat[nxt], b.cell[nxt], b.pinfo[nxt], b.pid[nxt], b.gate);
 }
 
 template <int W>
@@ -560,14 +577,15 @@ void launch_build_cell(const Buffers& b, int cur, const Geometry& g, const Phys&
     uint32_t blocks = (g.n_cells + W - 1) / W;
     if (blocks == 0) blocks = 1;
     k_build_cell<W><<<blocks, W * 32, 0, st>>>(b.pos[cur], b.pinfo[cur], b.start, b.cell_nfluid, b.scenes, g.n_cells,
-                                                b.status, b.nlist, b.ncount, ph.R2, ph.max_neibs, ph.stride);
+                                                b.status, b.nlist, b.ncount, ph.R2_list, ph.max_neibs, ph.stride,
+                                                b.gate);
 }
 
 template <int B>
 void launch_build_tpp(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
     k_build_tpp<B><<<grid_for(g.cap, B), B, 0, st>>>(b.pos[cur], b.cell[cur], b.pinfo[cur], b.start, b.cell_nfluid,
-                                                     b.scenes, b.status, b.nlist, b.ncount, ph.R2, ph.max_neibs,
-                                                     ph.stride);
+                                                     b.scenes, b.status, b.nlist, b.ncount, ph.R2_list, ph.max_neibs,
+                                                     ph.stride, b.gate);
 }
 
 const char* build_variant_name(int v) {
@@ -575,6 +593,47 @@ const char* build_variant_name(int v) {
                                                 "warp/cell x4 cells/CTA", "warp/cell x8 cells/CTA"};
     return v >= 0 && v < kBuildVariants ? names[v] : "?";
 }
+
+// skin list: the reorder wrote the sorted arrays to the other buffer; copy
+// them back (the step graph keeps one buffer) and record the offsets at the
+// build for the displacement check.
+__global__ void k_copyback(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                           const float* __restrict__ phat, const uint32_t* __restrict__ cell,
+                           const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ pid,
+                           const DevStatus* __restrict__ st, float4* __restrict__ pos_o, float4* __restrict__ vel_o,
+                           float* __restrict__ phat_o, uint32_t* __restrict__ cell_o, uint32_t* __restrict__ pinfo_o,
+                           uint32_t* __restrict__ pid_o, float4* __restrict__ pos_ref,
+                           const uint32_t* __restrict__ gate) {
+    if (gate && *gate == 0u) return;
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float4 p = pos[i];
+        pos_o[i] = p;
+        pos_ref[i] = p;
+        vel_o[i] = vel[i];
+        phat_o[i] = phat[i];
+        cell_o[i] = cell[i];
+        pinfo_o[i] = pinfo[i];
+        pid_o[i] = pid[i];
+    }
+}
+
+__global__ void k_force_rebuild(DevStatus* st) {
+    st->rebuild = 1u;
+    st->since = 0u;  // steps taken with the list built now
+    st->maxdisp2_bits = 0u;
+    st->builds += 1u;
+}
+
+void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
+    const int alt = cur ^ 1;
+    k_copyback<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.pos[alt], b.vel[alt], b.phat[alt], b.cell[alt],
+                                                            b.pinfo[alt], b.pid[alt], b.status, b.pos[cur],
+                                                            b.vel[cur], b.phat[cur], b.cell[cur], b.pinfo[cur],
+                                                            b.pid[cur], b.pos_ref, b.gate);
+}
+
+void launch_force_rebuild(const Buffers& b, cudaStream_t st) { k_force_rebuild<<<1, 1, 0, st>>>(b.status); }
 
 void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
     switch (ph.build_variant) {

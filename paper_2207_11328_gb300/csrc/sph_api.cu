@@ -39,7 +39,7 @@ struct sph_ctx {
     bool uploaded = false;
     bool need_dt0 = true;
     cudaStream_t cap_stream = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step, per buffer parity
     uint32_t graph_nodes = 0;
     size_t staging_bytes = 0;
 };
@@ -126,6 +126,11 @@ __global__ void k_set_status_n(DevStatus* st, uint32_t n) {
     st->upload_bits = 0;
     st->steps = 0ull;
     st->list_entries = 0ull;
+    st->interactions = 0ull;
+    st->rebuild = 1u;  // the upload builds the list
+    st->since = 0u;
+    st->maxdisp2_bits = 0u;
+    st->builds = 1u;
 }
 
 __global__ void k_reset_dyn(SceneDyn* dyn, uint32_t n_scenes) {
@@ -209,7 +214,8 @@ __global__ void k_download_neighbors(const uint32_t* __restrict__ nlist, const u
 
 int scene_from(const sph_params& p, const double origin[3], const double size[3], uint32_t periodic, double c0,
                uint32_t cell_offset, SceneDev& s, uint64_t& ncells) {
-    const double R = p.kernel_radius * p.h;
+    // cells of side >= the list radius (influence radius + skin in rebuild-every-k mode)
+    const double R = p.kernel_radius * p.h + (p.rebuild_every > 1 ? p.skin : 0.0);
     ncells = 1;
     for (int a = 0; a < 3; ++a) {
         if (!(size[a] > 0.0) || !std::isfinite(size[a]) || !std::isfinite(origin[a])) return SPH_ERR_ARG;
@@ -258,6 +264,8 @@ void drop_graphs(sph_ctx* c) {
         }
 }
 
+inline bool skin_mode(const sph_ctx* c) { return c->p.rebuild_every > 1; }
+
 int alloc_cells(sph_ctx* c) {
     const uint32_t nb = c->g.n_cells + 1;
     CK(cudaMalloc(&c->b.count, sizeof(uint32_t) * nb));
@@ -303,43 +311,59 @@ void enqueue_sort(sph_ctx* c, cudaStream_t st) {
 }
 
 void enqueue_build(sph_ctx* c, cudaStream_t st) {
+    if (skin_mode(c)) {
+        // gated by status->rebuild; the sorted arrays come back to the same buffer
+        launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+        launch_scan(c->b, c->g, st);
+        launch_scatter(c->b, c->cur, c->g, st);
+        launch_reorder(c->b, c->cur, c->g, st);
+        launch_copyback(c->b, c->cur, c->g, st);
+        launch_build(c->b, c->cur, c->g, c->ph, st);
+        return;
+    }
     enqueue_sort(c, st);
     launch_build(c->b, c->cur, c->g, c->ph, st);
 }
 
 void enqueue_step(sph_ctx* c, cudaStream_t st) {
-    launch_dt(c->b, c->g, c->ph, 1, st);
+    launch_dt(c->b, c->g, c->ph, 1, st);  // (skin list: decides whether the pipeline runs)
     enqueue_build(c, st);
     launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st);
     launch_forces(c->b, c->cur, c->g, c->ph, kCorrect, 0, st);
 }
 
+int capture_one(sph_ctx* c, int par, cudaGraphExec_t* out) {
+    c->cur = par;
+    cudaGraph_t gr = nullptr;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    enqueue_step(c, c->cap_stream);
+    CK(cudaStreamEndCapture(c->cap_stream, &gr));
+    size_t nn = 0;
+    cudaGraphGetNodes(gr, nullptr, &nn);
+    c->graph_nodes = (uint32_t)nn;
+    cudaError_t e = cudaGraphInstantiate(out, gr, 0);
+    cudaGraphDestroy(gr);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "sph: graph instantiate failed: %s\n", cudaGetErrorString(e));
+        return SPH_ERR_CUDA;
+    }
+    return SPH_OK;
+}
+
+// one graph per buffer parity (the reorder switches buffers every step); a
+// skin list keeps one buffer, so one graph serves every step
 int capture_graphs(sph_ctx* c) {
     const int cur0 = c->cur;
-    for (int par = 0; par < 2; ++par) {
-        c->cur = par;
-        cudaGraph_t gr = nullptr;
-        CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
-        enqueue_step(c, c->cap_stream);
-        CK(cudaStreamEndCapture(c->cap_stream, &gr));
-        size_t nn = 0;
-        cudaGraphGetNodes(gr, nullptr, &nn);
-        c->graph_nodes = (uint32_t)nn;
-        cudaError_t e = cudaGraphInstantiate(&c->graph[par], gr, 0);
-        cudaGraphDestroy(gr);
-        if (e != cudaSuccess) {
-            std::fprintf(stderr, "sph: graph instantiate failed: %s\n", cudaGetErrorString(e));
-            c->cur = cur0;
-            return SPH_ERR_CUDA;
-        }
-    }
+    int rc = capture_one(c, cur0, &c->graph[cur0]);
+    if (rc == SPH_OK && !skin_mode(c)) rc = capture_one(c, cur0 ^ 1, &c->graph[cur0 ^ 1]);
     c->cur = cur0;
-    return SPH_OK;
+    return rc;
 }
 
 int error_from_bits(uint32_t bits) {
     if (bits & SPH_EBIT_NEIB_OVERFLOW) return SPH_ERR_NEIB_OVERFLOW;
     if (bits & SPH_EBIT_NONFINITE) return SPH_ERR_NONFINITE;
+    if (bits & SPH_EBIT_SKIN) return SPH_ERR_SKIN;
     if (bits & SPH_EBIT_TIMEOUT) return SPH_ERR_TIMEOUT;
     return SPH_OK;
 }
@@ -394,6 +418,7 @@ const char* sph_strerror(int code) {
         case SPH_ERR_NONFINITE: return "non-finite value in the particle state";
         case SPH_ERR_TIMEOUT: return "device wait timed out";
         case SPH_ERR_STATE: return "call out of order";
+        case SPH_ERR_SKIN: return "a particle moved more than skin/2 since the last neighbour-list build";
         default: return "unknown error";
     }
 }
@@ -404,7 +429,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     if (!(p->h > 0) || !(p->rho0 > 0) || !(p->c0 > 0) || !(gm >= 1 && gm <= 8 && gm == std::floor(gm)) ||
         !(p->kernel_radius > 0) || !(p->cfl > 0) || p->max_particles == 0 || p->max_particles > kMaxParticles ||
         p->max_neibs < 8 || p->max_neibs > 1024 || (p->visc_model != SPH_VISC_ARTIFICIAL && p->visc_model != SPH_VISC_LAMINAR) ||
-        !(p->alpha >= 0) || !(p->nu >= 0))
+        !(p->alpha >= 0) || !(p->nu >= 0) || !(p->skin >= 0) || (p->rebuild_every > 1 && !(p->skin > 0)))
         return SPH_ERR_ARG;
     sph_ctx* c = new (std::nothrow) sph_ctx();
     if (!c) return SPH_ERR_ARG;
@@ -417,6 +442,11 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.h = (float)h;
     ph.inv_h = (float)(1.0 / h);
     ph.R2 = (float)(R * R);
+    const double Rl = R + (p->rebuild_every > 1 ? p->skin : 0.0);
+    ph.R2_list = (float)(Rl * Rl);
+    ph.skin_lim2 = (float)(0.25 * p->skin * p->skin);
+    ph.skin_trig2 = (float)(0.0625 * p->skin * p->skin);
+    ph.rebuild_every = p->rebuild_every;
     ph.aF = (float)(105.0 / (128.0 * 3.14159265358979323846 * h * h * h * h * h));
     ph.rho0 = (float)p->rho0;
     ph.inv_rho0 = (float)(1.0 / p->rho0);
@@ -436,7 +466,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.max_neibs = p->max_neibs;
     ph.gamma_i = (int)gm;
     ph.build_variant = 0;
-    ph.forces_block = 128;
+    ph.forces_variant = 1;
     const uint32_t cap = p->max_particles;
     ph.stride = (uint32_t)align_up(cap, 32);
     c->g.cap = cap;
@@ -461,6 +491,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
              alloc((void**)&b.cell[k], sizeof(uint32_t) * cap) && alloc((void**)&b.pinfo[k], sizeof(uint32_t) * cap) &&
              alloc((void**)&b.pid[k], sizeof(uint32_t) * cap);
     }
+    if (p->rebuild_every > 1) ok = ok && alloc((void**)&b.pos_ref, sizeof(float4) * cap);
     ok = ok && alloc((void**)&b.pos_s, sizeof(float4) * cap) && alloc((void**)&b.vel_s, sizeof(float4) * cap) &&
          alloc((void**)&b.phat_s, sizeof(float) * cap) &&
          alloc((void**)&b.force, sizeof(float4) * cap) && alloc((void**)&b.key, sizeof(uint32_t) * cap) &&
@@ -476,6 +507,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
         return SPH_ERR_CUDA;
     }
     cudaMemset(b.status, 0, sizeof(DevStatus));
+    b.gate = p->rebuild_every > 1 ? &b.status->rebuild : nullptr;
     cudaMemset(b.force, 0, sizeof(float4) * cap);
     cudaMemset(b.ncount, 0, sizeof(uint32_t) * cap);
     if (cudaDeviceSynchronize() != cudaSuccess) {
@@ -539,6 +571,7 @@ int sph_upload_device(sph_ctx* c, uint32_t n, const double* pos, const float* ve
 int sph_build_neighbors(sph_ctx* c, void* stream) {
     if (!c) return SPH_ERR_ARG;
     if (!c->uploaded) return SPH_ERR_STATE;
+    if (skin_mode(c)) launch_force_rebuild(c->b, S(stream));
     enqueue_build(c, S(stream));
     CK(cudaGetLastError());
     return SPH_OK;
@@ -562,18 +595,18 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
         CK(cudaGetLastError());
         c->need_dt0 = false;
     }
-    if (!c->graph[0]) {
+    if (!c->graph[c->cur]) {
         int rc = capture_graphs(c);
         if (rc) return rc;
     }
     for (uint32_t s = 0; s < nsteps; ++s) {
         CK(cudaGraphLaunch(c->graph[c->cur], st));
-        c->cur ^= 1;
+        if (!skin_mode(c)) c->cur ^= 1;
     }
     return SPH_OK;
 }
 
-int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_block) {
+int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_variant) {
     if (!c) return SPH_ERR_ARG;
     if (!c->uploaded) return SPH_ERR_STATE;
     cudaStream_t st = S(stream);
@@ -594,6 +627,7 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_block
     // all variants write the same list, so the state is unchanged by tuning
     int best_v = c->ph.build_variant;
     float best = 3.4e38f;
+    if (skin_mode(c)) launch_force_rebuild(c->b, st);  // the gated build must run while timed
     for (int v = 0; v < kBuildVariants; ++v) {
         c->ph.build_variant = v;
         const float ms = time_ms([&] { launch_build(c->b, c->cur, c->g, c->ph, st); });
@@ -604,30 +638,31 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_block
     }
     c->ph.build_variant = best_v;
     launch_build(c->b, c->cur, c->g, c->ph, st);
-    // force kernels: threads per block
-    const int blocks[3] = {64, 128, 256};
-    int best_b = c->ph.forces_block;
+    // force kernels: threads per block and register cap
+    int best_f = c->ph.forces_variant;
     best = 3.4e38f;
-    for (int k = 0; k < 3; ++k) {
-        c->ph.forces_block = blocks[k];
+    for (int v = 0; v < kForcesVariants; ++v) {
+        c->ph.forces_variant = v;
         const float ms = time_ms([&] { launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, st); });
         if (ms < best) {
             best = ms;
-            best_b = blocks[k];
+            best_f = v;
         }
     }
-    c->ph.forces_block = best_b;
+    c->ph.forces_variant = best_f;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     drop_graphs(c);  // captured launches carry the old shapes
     if (build_variant) *build_variant = best_v;
-    if (forces_block) *forces_block = best_b;
+    if (forces_variant) *forces_variant = best_f;
     return SPH_OK;
 }
 
 const char* sph_build_variant_name(int variant) { return build_variant_name(variant); }
+
+const char* sph_forces_variant_name(int variant) { return forces_variant_name(variant); }
 
 namespace {
 
@@ -716,7 +751,7 @@ int sph_set_alpha(sph_ctx* c, double alpha) {
 int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out) {
     if (!c || T == 0 || K == 0 || T % K != 0) return SPH_ERR_ARG;
     if (!c->uploaded) return SPH_ERR_STATE;
-    if (c->g.n_scenes != 1) return SPH_ERR_ARG;
+    if (c->g.n_scenes != 1 || skin_mode(c)) return SPH_ERR_ARG;  // one scene, list rebuilt every step
     cudaStream_t st = S(stream);
     free_tape(c);
     AdjTape& t = c->tape;
@@ -849,7 +884,10 @@ int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_m
         launch_scatter(c->b, c->cur, c->g, st);
         cudaEventRecord(ev[4], st);
         launch_reorder(c->b, c->cur, c->g, st);
-        c->cur ^= 1;
+        if (skin_mode(c))
+            launch_copyback(c->b, c->cur, c->g, st);
+        else
+            c->cur ^= 1;
         cudaEventRecord(ev[5], st);
         launch_build(c->b, c->cur, c->g, c->ph, st);
         cudaEventRecord(ev[6], st);
@@ -1041,6 +1079,8 @@ int sph_get_stats(sph_ctx* c, sph_stats* out, void* stream) {
     out->n_cells = c->g.n_cells;
     out->kernels_per_step = c->graph_nodes;
     out->list_entries = hs.list_entries;
+    out->interactions = hs.interactions;
+    out->builds = hs.builds;
     return error_from_bits(hs.error_bits);
 }
 
@@ -1083,6 +1123,7 @@ void sph_destroy(sph_ctx* c) {
         cudaFree(b.pinfo[k]);
         cudaFree(b.pid[k]);
     }
+    cudaFree(b.pos_ref);
     cudaFree(b.pos_s);
     cudaFree(b.vel_s);
     cudaFree(b.phat_s);

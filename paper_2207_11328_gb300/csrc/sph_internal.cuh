@@ -59,9 +59,13 @@ struct DevStatus {
     uint32_t max_neibs_seen; // largest count of the last build
     uint32_t error_bits;     // SPH_EBIT_*
     uint32_t upload_bits;    // validation of the last upload
-    uint32_t pad[2];
+    uint32_t rebuild;        // skin list: run the neighbour pipeline this step (gate of its kernels)
+    uint32_t since;          // skin list: steps taken with the current list
     unsigned long long steps;
     unsigned long long list_entries;  // cumulative neighbour-list entries written
+    unsigned long long interactions;  // pairs within the influence radius (counted passes)
+    uint32_t maxdisp2_bits;  // skin list: max displacement^2 since the build (float bits)
+    uint32_t builds;         // neighbour-list builds since upload (the upload's included)
 };
 
 // upload validation bits
@@ -69,7 +73,11 @@ constexpr uint32_t kUpBadArg = 1u, kUpOutOfDomain = 2u, kUpNonFinite = 4u;
 
 // Kernel-uniform physics, passed by value (lands in the constant bank).
 struct Phys {
-    float h, inv_h, R2;      // R2 = (kernel_radius*h)^2
+    float h, inv_h, R2;      // R2 = (kernel_radius*h)^2: interactions
+    float R2_list;           // (kernel_radius*h + skin)^2: neighbour list
+    float skin_lim2;         // (skin/2)^2: largest displacement^2 the list tolerates
+    float skin_trig2;        // (skin/4)^2: displacement^2 that triggers a rebuild
+    uint32_t rebuild_every;  // > 1: skin list, rebuilt at least every rebuild_every steps
     float aF;                // F(q) = aF (q-2)^3, aF = 105/(128 pi h^5)
     float rho0, inv_rho0;
     float eps_h2;            // 0.01 h^2
@@ -83,11 +91,13 @@ struct Phys {
     uint32_t n_scenes;
     int gamma_i;             // EOS exponent (integer)
     int build_variant;       // neighbour-build kernel variant (autotuned), see build_variant_name
-    int forces_block;        // threads per block of the force kernels (autotuned)
+    int forces_variant;      // launch shape of the force kernels (autotuned), see forces_variant_name
 };
 
 constexpr int kBuildVariants = 5;
 const char* build_variant_name(int v);
+constexpr int kForcesVariants = 5;
+const char* forces_variant_name(int v);
 
 // P/rho^2 of Cole's EOS from delta = rho/rho0 - 1 (binomial form, no
 // cancellation near rest): phat_coef * delta * sum_k C(gamma,k) delta^(k-1) / (1+delta)^2.
@@ -126,6 +136,8 @@ struct Buffers {
     uint32_t* pinfo[2];
     uint32_t* pid[2];
     float* phat[2];          // P/rho^2 per particle, same order as pos/vel
+    float4* pos_ref;         // offsets at the last list build (rebuild_every > 1), else null
+    const uint32_t* gate;    // &status->rebuild for a skin list (pipeline kernels skip when 0), else null
     float4* pos_s;           // predicted state
     float4* vel_s;
     float* phat_s;
@@ -185,8 +197,13 @@ void launch_adj_store(const AdjBuffers& a, uint32_t n, float* xbar, float* ubar,
 
 // forces.cu
 enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };
+// With a skin list (pos_ref allocated) the kernels skip pairs beyond the
+// cutoff, the first pass counts the pairs within it (DevStatus.interactions)
+// and the corrector checks the displacement since the build.
 void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
                    int acc_dt, cudaStream_t st);
+void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_force_rebuild(const Buffers& b, cudaStream_t st);
 void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st);
 
 }  // namespace sphg
