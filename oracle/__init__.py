@@ -5,10 +5,13 @@ baseline leg of ``bench.py`` may import this package.  The CUDA library never
 calls it and shares no code with it.
 
 Functions and the passages they follow (arXiv 2207.11328):
-  kernel_W / kernel_F   Wendland C2 kernel listing (Section 4) + unit integral (Section 2.1)
+  kernel_W / kernel_F   kernel-templates listing (Section 4), Table 1 kernels + unit integral (Section 2.1)
   eos                   Cole equation of state (Section 2.1), binomial form
   neighbors             neighbour sets 0 < r < 2h (Section 2.3), brute force or binning
-  rhs / rhs_sample      golden-rule continuity + momentum (Section 2.1, readings C1-C5)
+  rhs / rhs_sample      golden-rule continuity + momentum (Section 2.1, readings C1-C5), with the
+                        Table 1 options: formulation 2, Morris / Monaghan / Espanol-Revenga
+                        viscosity and averaging operators (Section 3), Molteni-Colagrossi
+                        density diffusion (reading D1)
   step                  predictor-corrector + CFL dt (readings C6, C7)
   energy                kinetic + internal + potential energy (invariant check)
   loss_jvp              loss after T steps and its directional derivative (dual numbers)
@@ -52,7 +55,10 @@ class Params(ctypes.Structure):
                 ("alpha", ctypes.c_double), ("nu", ctypes.c_double),
                 ("g", ctypes.c_double * 3), ("cfl", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3),
-                ("periodic_mask", ctypes.c_uint32), ("pad1", ctypes.c_uint32)]
+                ("periodic_mask", ctypes.c_uint32), ("pad1", ctypes.c_uint32),
+                ("kernel_type", ctypes.c_int32), ("formulation", ctypes.c_int32),
+                ("visc_avg", ctypes.c_int32), ("ddiff", ctypes.c_int32),
+                ("ddiff_coef", ctypes.c_double), ("zeta", ctypes.c_double)]
 
 
 def _configure(lib):
@@ -65,6 +71,9 @@ def _configure(lib):
     lib.ora_kernel_W.argtypes = [ctypes.c_double, ctypes.c_double]
     lib.ora_kernel_F.restype = ctypes.c_double
     lib.ora_kernel_F.argtypes = [ctypes.c_double, ctypes.c_double]
+    for f in (lib.ora_kernel_Wk, lib.ora_kernel_Fk):
+        f.restype = ctypes.c_double
+        f.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
     lib.ora_eos.restype = ctypes.c_double
     lib.ora_eos.argtypes = [P, ctypes.c_double]
     lib.ora_neighbors.restype = ctypes.c_int64
@@ -126,7 +135,9 @@ def params(scene=None, **kw) -> Params:
         src = dict(dp=scene.dp, h=scene.h, kernel_radius=scene.kernel_radius, rho0=scene.rho0,
                    c0=scene.c0, gamma=float(scene.gamma), visc_model=scene.visc, alpha=scene.alpha,
                    nu=scene.nu, g=scene.g, cfl=scene.cfl, dt_fixed=scene.dt_fixed,
-                   origin=scene.origin, size=scene.size, periodic_mask=scene.periodic)
+                   origin=scene.origin, size=scene.size, periodic_mask=scene.periodic,
+                   kernel_type=scene.kernel_type, formulation=scene.formulation, visc_avg=scene.visc_avg,
+                   ddiff=scene.ddiff, ddiff_coef=scene.ddiff_coef, zeta=scene.zeta)
     src.update(kw)
     p = Params()
     for k, v in src.items():
@@ -139,12 +150,18 @@ def params(scene=None, **kw) -> Params:
     return p
 
 
-def kernel_W(r, h):
-    return _load().ora_kernel_W(float(r), float(h))
+def kernel_W(r, h, kernel=0, radius=2.0):
+    """W(r) of a Table-1 kernel (0 Wendland C2, 1 cubic spline, 2 quadratic, 3 Gaussian cut at radius*h)."""
+    if kernel == 0:
+        return _load().ora_kernel_W(float(r), float(h))
+    return _load().ora_kernel_Wk(int(kernel), float(radius), float(r), float(h))
 
 
-def kernel_F(r, h):
-    return _load().ora_kernel_F(float(r), float(h))
+def kernel_F(r, h, kernel=0, radius=2.0):
+    """F(r) = (1/r) dW/dr of the same kernels."""
+    if kernel == 0:
+        return _load().ora_kernel_F(float(r), float(h))
+    return _load().ora_kernel_Fk(int(kernel), float(radius), float(r), float(h))
 
 
 def eos(p: Params, delta):

@@ -28,7 +28,7 @@ extern "C" {
 typedef struct {
     double dp, h, kernel_radius;   /* influence radius R = kernel_radius*h (Section 2.1, compact support) */
     double rho0, c0, gamma;        /* Cole/Tait equation of state, Section 2.1 */
-    int32_t visc_model;            /* 0 artificial (Monaghan), 1 laminar (Morris, kinematic, harmonic) */
+    int32_t visc_model;            /* 0 artificial (Monaghan), laminar: 1 Morris, 2 Monaghan, 3 Espanol & Revenga */
     int32_t pad0;
     double alpha, nu;              /* artificial-viscosity coefficient / kinematic viscosity */
     double g[3];                   /* body force, fluid only */
@@ -36,6 +36,13 @@ typedef struct {
     double origin[3], size[3];     /* domain; periodic axes wrap with period size[axis] */
     uint32_t periodic_mask;        /* bit0 x, bit1 y, bit2 z */
     uint32_t pad1;
+    /* model options of Table 1 (0 everywhere = the model above) */
+    int32_t kernel_type;           /* 0 Wendland C2, 1 cubic spline, 2 quadratic, 3 Gaussian */
+    int32_t formulation;           /* 0 eqs. mass-cont-sph1/ns-sph1, 1 eqs. mass-cont-sph2/ns-sph2 */
+    int32_t visc_avg;              /* laminar models: 0 harmonic, 1 arithmetic, 2 geometric mean */
+    int32_t ddiff;                 /* density diffusion: 0 none, 1 Molteni & Colagrossi */
+    double ddiff_coef;             /* its coefficient xi */
+    double zeta;                   /* kinematic bulk viscosity (Espanol & Revenga model) */
 } ora_params;
 
 }  // extern "C"
@@ -61,9 +68,11 @@ inline Dual operator/(Dual a, Dual b) { return Dual(a.v / b.v, (a.d * b.v - a.v 
 inline Dual& operator+=(Dual& a, Dual b) { a = a + b; return a; }
 inline Dual& operator-=(Dual& a, Dual b) { a = a - b; return a; }
 inline Dual sqrt(Dual a) { double s = std::sqrt(a.v); return Dual(s, a.d / (2.0 * s)); }
+inline Dual exp(Dual a) { double e = std::exp(a.v); return Dual(e, a.d * e); }
 
 inline double pv(double a) { return a; }
 inline double pv(const Dual& a) { return a.v; }
+using std::exp;
 using std::sqrt;
 
 /* ------------------------------------------------------------------ */
@@ -87,6 +96,76 @@ T kernel_F(T r, double h) {
     if (pv(q) >= 2.0) return T(0.0);
     T qm2 = q - T(2.0);
     return T(105.0 / (128.0 * kPi * h * h * h * h * h)) * qm2 * qm2 * qm2;
+}
+
+/* ------------------------------------------------------------------ */
+/* The other smoothing kernels of Table 1 and of the kernel-templates   */
+/* listing (Section 4), 3D.  Each is W = a_W w(q) with F = (1/r) dW/dr; */
+/* a_W follows from the unit integral 4 pi h^3 a_W int w(q) q^2 dq = 1: */
+/*  cubic spline  w = 1 - 3/2 q^2 + 3/4 q^3 (q<1), (2-q)^3/4 (q<2)     */
+/*                a_W = 1/(pi h^3)                                       */
+/*  quadratic     w = (2-q)^2 (q<2),   a_W = 15/(64 pi h^3)             */
+/*  Gaussian      w = exp(-q^2) - exp(-Q^2) (q<Q, Q = kernel_radius),   */
+/*                a_W = 1/(4 pi h^3 S(Q)),                               */
+/*                S(Q) = sqrt(pi)/4 erf(Q) - (Q/2 + Q^3/3) exp(-Q^2)     */
+/* ------------------------------------------------------------------ */
+double gaussian_S(double Q) {
+    return std::sqrt(kPi) / 4.0 * std::erf(Q) - (Q / 2.0 + Q * Q * Q / 3.0) * std::exp(-Q * Q);
+}
+
+template <class T>
+T kernel_Wk(int type, double Q, T r, double h) {
+    const double h3 = h * h * h;
+    T q = r / h;
+    if (type == 1) {
+        if (pv(q) >= 2.0) return T(0.0);
+        if (pv(q) < 1.0) return T(1.0 / (kPi * h3)) * (T(1.0) - q * q * 1.5 + q * q * q * 0.75);
+        T t = T(2.0) - q;
+        return T(1.0 / (kPi * h3)) * t * t * t * 0.25;
+    }
+    if (type == 2) {
+        if (pv(q) >= 2.0) return T(0.0);
+        T t = T(2.0) - q;
+        return T(15.0 / (64.0 * kPi * h3)) * t * t;
+    }
+    if (type == 3) {
+        if (pv(q) >= Q) return T(0.0);
+        return T(1.0 / (4.0 * kPi * h3 * gaussian_S(Q))) * (exp(-(q * q)) - T(std::exp(-Q * Q)));
+    }
+    return kernel_W(r, h);
+}
+
+/* F = (1/r) dW/dr = a_W w'(q) / (h^2 q):
+ *  cubic spline  (-3 + 9/4 q) (q<1),  -3/4 (2-q)^2 / q (q<2),  times 1/(pi h^5)
+ *  quadratic     (q - 2)/q,  times 15/(32 pi h^5)
+ *  Gaussian      -exp(-q^2), times 1/(2 pi h^5 S(Q))   (no smooth cut at Q) */
+template <class T>
+T kernel_Fk(int type, double Q, T r, double h) {
+    const double h5 = h * h * h * h * h;
+    T q = r / h;
+    if (type == 1) {
+        if (pv(q) >= 2.0) return T(0.0);
+        if (pv(q) < 1.0) return T(1.0 / (kPi * h5)) * (q * 2.25 - T(3.0));
+        T t = T(2.0) - q;
+        return T(1.0 / (kPi * h5)) * (t * t * -0.75) / q;
+    }
+    if (type == 2) {
+        if (pv(q) >= 2.0) return T(0.0);
+        return T(15.0 / (32.0 * kPi * h5)) * (q - T(2.0)) / q;
+    }
+    if (type == 3) {
+        if (pv(q) >= Q) return T(0.0);
+        return -T(1.0 / (2.0 * kPi * h5 * gaussian_S(Q))) * exp(-(q * q));
+    }
+    return kernel_F(r, h);
+}
+
+/* Averaging operator of Table 1 for two positive values. */
+template <class T>
+T average(int op, T a, T b) {
+    if (op == 1) return (a + b) * 0.5;
+    if (op == 2) return sqrt(a * b);
+    return a * b * 2.0 / (a + b);
 }
 
 /* ------------------------------------------------------------------ */
@@ -260,6 +339,21 @@ void neighbors_grid(const ora_params& P, int n, const double* x, Nbrs& out) {
 /*  mu_ij = u_ij.x_ij / (r^2 + 0.01 h^2),  rhobar = (rho_i+rho_j)/2 (C4)*/
 /*  Dynamic boundary particles (C5): velocity zero, positions fixed,   */
 /*  continuity and EOS as fluid, no momentum equation.                 */
+/*                                                                      */
+/* Model options (Table 1; Section 3, viscous-term specialisations):   */
+/*  formulation 2 (eqs. mass-cont-sph2, ns-sph2; readings C1, C2):     */
+/*    drho_i/dt = + sum_j (rho_i/rho_j) m_j u_ij.x_ij F_ij              */
+/*    pressure    - sum_j m_j ((P_i + P_j)/(rho_i rho_j) + Pi_ij) x_ij F_ij */
+/*  laminar viscous models, omega_ij = m_j/(rho_i rho_j), mubar_ij the */
+/*  average of mu = rho nu (zetabar of rho zeta):                       */
+/*    Morris    + sum_j omega 2 mubar F u_ij                             */
+/*    Monaghan  + K sum_j omega 2 mubar F (x.u/x.x) x_ij, K = 5 (C11)    */
+/*    Espanol & Revenga + sum_j omega F ((5/3 mubar - zetabar) u_ij      */
+/*                         + 5 (mubar/3 + zetabar) (x.u/x.x) x_ij)       */
+/*  density diffusion, Molteni & Colagrossi (reading D1): fluid pairs  */
+/*    + xi h c0 sum_j psi_ij . grad_i W_ij m_j/rho_j,                   */
+/*    psi_ij = 2 (rho_j - rho_i) x_ji / |x_ij|^2, grad_i W_ij = x_ij F_ij */
+/*    = + 2 xi h c0 sum_j (rho_i - rho_j) F_ij m_j/rho_j                 */
 /* ------------------------------------------------------------------ */
 template <class T>
 struct State {
@@ -276,6 +370,7 @@ void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* d
     double mag_a = 0.0, mag_d = 0.0;
     const double h = P.h;
     const bool fluid_i = type[i] == 0;
+    const bool form2 = P.formulation == 1;
     T ui[3];
     for (int c = 0; c < 3; ++c) ui[c] = fluid_i ? u[3 * i + c] : T(0.0);
     T drho(0.0), a[3] = {T(0.0), T(0.0), T(0.0)};
@@ -286,15 +381,22 @@ void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* d
         T r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
         if (!(pv(r2) > 0.0)) continue;
         T r = sqrt(r2);
-        T F = kernel_F(r, h);
+        T F = kernel_Fk(P.kernel_type, P.kernel_radius, r, h);
         const bool fluid_j = type[j] == 0;
         T uij[3];
         for (int c = 0; c < 3; ++c) uij[c] = ui[c] - (fluid_j ? u[3 * j + c] : T(0.0));
         T udotx = uij[0] * d[0] + uij[1] * d[1] + uij[2] * d[2];
-        drho += T(m[j]) * udotx * F;
-        if (mag) mag_d += std::fabs(pv(T(m[j]) * udotx * F));
+        T mc = form2 ? T(m[j]) * rho[i] / rho[j] : T(m[j]);
+        drho += mc * udotx * F;
+        if (mag) mag_d += std::fabs(pv(mc * udotx * F));
+        if (P.ddiff == 1 && fluid_i && fluid_j) {
+            T dd = T(2.0 * P.ddiff_coef * h * P.c0) * (rho[i] - rho[j]) * F * T(m[j]) / rho[j];
+            drho += dd;
+            if (mag) mag_d += std::fabs(pv(dd));
+        }
         if (!fluid_i) continue;
-        T bracket = phat[i] + phat[j];
+        T bracket = form2 ? (eos_pressure(delta[i], P) + eos_pressure(delta[j], P)) / (rho[i] * rho[j])
+                          : phat[i] + phat[j];
         if (P.visc_model == 0 && pv(udotx) < 0.0) {
             T mu = udotx / (r2 + T(0.01 * h * h));
             T rhobar = (rho[i] + rho[j]) * 0.5;
@@ -303,10 +405,23 @@ void particle_rhs(const ora_params& P, int i, const T* x, const T* u, const T* d
         T coef = T(m[j]) * bracket * F;
         for (int c = 0; c < 3; ++c) a[c] -= coef * d[c];
         if (mag) mag_a += std::fabs(pv(coef)) * std::sqrt(pv(r2));
-        if (P.visc_model == 1) {
-            T lam = T(4.0 * P.nu * m[j]) * F / (rho[i] + rho[j]);
-            for (int c = 0; c < 3; ++c) a[c] += lam * uij[c];
-            if (mag) mag_a += std::fabs(pv(lam)) * std::sqrt(pv(uij[0] * uij[0] + uij[1] * uij[1] + uij[2] * uij[2]));
+        if (P.visc_model >= 1) {
+            T omega = T(m[j]) / (rho[i] * rho[j]);
+            T mubar = average(P.visc_avg, rho[i], rho[j]) * P.nu;
+            T lu(0.0), lx(0.0);  /* a += lu * u_ij + lx * x_ij */
+            if (P.visc_model == 1) {
+                lu = omega * 2.0 * mubar * F;
+            } else if (P.visc_model == 2) {
+                lx = omega * 2.0 * mubar * F * udotx / r2 * 5.0;
+            } else {
+                T zetabar = average(P.visc_avg, rho[i], rho[j]) * P.zeta;
+                lu = omega * F * (mubar * (5.0 / 3.0) - zetabar);
+                lx = omega * F * (mubar / 3.0 + zetabar) * 5.0 * udotx / r2;
+            }
+            for (int c = 0; c < 3; ++c) a[c] += lu * uij[c] + lx * d[c];
+            if (mag)
+                mag_a += std::fabs(pv(lu)) * std::sqrt(pv(uij[0] * uij[0] + uij[1] * uij[1] + uij[2] * uij[2])) +
+                         std::fabs(pv(lx)) * std::sqrt(pv(r2));
         }
     }
     if (mag) {
@@ -346,7 +461,7 @@ double cfl_dt(const ora_params& P, int n, const double* a, const uint8_t* type) 
     }
     double dt = P.h / P.c0;
     if (amax2 > 0.0) dt = std::min(dt, std::sqrt(P.h / std::sqrt(amax2)));
-    if (P.visc_model == 1 && P.nu > 0.0) dt = std::min(dt, P.h * P.h / P.nu);
+    if (P.visc_model >= 1 && P.nu > 0.0) dt = std::min(dt, P.h * P.h / P.nu);
     return P.cfl * dt;
 }
 
@@ -424,6 +539,9 @@ extern "C" {
 
 double ora_kernel_W(double r, double h) { return kernel_W<double>(r, h); }
 double ora_kernel_F(double r, double h) { return kernel_F<double>(r, h); }
+/* Any kernel of Table 1: type as ora_params.kernel_type, Q = kernel_radius (Gaussian cut). */
+double ora_kernel_Wk(int type, double Q, double r, double h) { return kernel_Wk<double>(type, Q, r, h); }
+double ora_kernel_Fk(int type, double Q, double r, double h) { return kernel_Fk<double>(type, Q, r, h); }
 
 double ora_eos(const ora_params* P, double delta) { return eos_pressure<double>(delta, *P); }
 

@@ -54,6 +54,15 @@ class Scene:
     periodic: int          # bit0 x, bit1 y, bit2 z
     dt_fixed: float = 0.0
     kernel_radius: float = 2.0
+    # model options (Table 1): kernel 0 Wendland C2 / 1 cubic spline / 2 quadratic /
+    # 3 Gaussian; formulation 0 or 1 (the paper's second form); laminar averaging
+    # 0 harmonic / 1 arithmetic / 2 geometric; density diffusion 0 none / 1 Molteni-Colagrossi
+    kernel_type: int = 0
+    formulation: int = 0
+    visc_avg: int = 0
+    ddiff: int = 0
+    ddiff_coef: float = 0.0
+    zeta: float = 0.0
     # batched scenes: per-scene geometry and sound speed (None for a single scene)
     scenes: list | None = None
 

@@ -13,11 +13,12 @@ import oracle
 from paper_2207_11328_gb300 import scenes
 from tests import test_oracle_integration as ti
 from tests import test_oracle_kernel_eos as tk
+from tests import test_oracle_models as tm
 from tests import test_oracle_neighbors as tn
 from tests import test_oracle_physics as tp
 
 MUTANTS = [
-    ("continuity sign", "drho += T(m[j]) * udotx * F;", "drho -= T(m[j]) * udotx * F;"),
+    ("continuity sign", "drho += mc * udotx * F;", "drho -= mc * udotx * F;"),
     ("pressure term without m_j", "T coef = T(m[j]) * bracket * F;", "T coef = bracket * F;"),
     ("pressure sign", "for (int c = 0; c < 3; ++c) a[c] -= coef * d[c];",
      "for (int c = 0; c < 3; ++c) a[c] += coef * d[c];"),
@@ -27,9 +28,27 @@ MUTANTS = [
     ("EOS binomial index", "binom = binom * (double)(gam - k + 1) / (double)k;",
      "binom = binom * (double)(gam - k) / (double)k;"),
     ("EOS constant B", "double B = P.rho0 * P.c0 * P.c0 / P.gamma;", "double B = P.rho0 * P.c0 / P.gamma;"),
-    ("laminar coefficient", "T lam = T(4.0 * P.nu * m[j])", "T lam = T(2.0 * P.nu * m[j])"),
-    ("laminar sign", "for (int c = 0; c < 3; ++c) a[c] += lam * uij[c];",
-     "for (int c = 0; c < 3; ++c) a[c] -= lam * uij[c];"),
+    ("laminar coefficient", "lu = omega * 2.0 * mubar * F;", "lu = omega * mubar * F;"),
+    ("laminar sign", "a[c] += lu * uij[c] + lx * d[c];", "a[c] -= lu * uij[c] + lx * d[c];"),
+    ("harmonic mean", "return a * b * 2.0 / (a + b);", "return a * b / (a + b);"),
+    ("geometric mean", "if (op == 2) return sqrt(a * b);", "if (op == 2) return (a + b) * 0.5;"),
+    ("Monaghan K", "lx = omega * 2.0 * mubar * F * udotx / r2 * 5.0;", "lx = omega * 2.0 * mubar * F * udotx / r2 * 10.0;"),
+    ("Espanol-Revenga shear coefficient", "mubar * (5.0 / 3.0) - zetabar", "mubar * (4.0 / 3.0) - zetabar"),
+    ("Espanol-Revenga bulk sign", "mubar * (5.0 / 3.0) - zetabar", "mubar * (5.0 / 3.0) + zetabar"),
+    ("Espanol-Revenga projection", "(mubar / 3.0 + zetabar) * 5.0 * udotx / r2", "(mubar / 3.0 + zetabar) * 3.0 * udotx / r2"),
+    ("formulation 2 density ratio", "T mc = form2 ? T(m[j]) * rho[i] / rho[j] : T(m[j]);",
+     "T mc = form2 ? T(m[j]) * rho[j] / rho[i] : T(m[j]);"),
+    ("formulation 2 pressure denominator", "eos_pressure(delta[j], P)) / (rho[i] * rho[j])",
+     "eos_pressure(delta[j], P)) / (rho[i] * rho[i])"),
+    ("diffusion sign", "(rho[i] - rho[j]) * F", "(rho[j] - rho[i]) * F"),
+    ("diffusion volume", "* F * T(m[j]) / rho[j];", "* F * T(m[j]) / rho[i];"),
+    ("diffusion factor 2", "T(2.0 * P.ddiff_coef * h * P.c0)", "T(P.ddiff_coef * h * P.c0)"),
+    ("diffusion through boundary", "if (P.ddiff == 1 && fluid_i && fluid_j) {", "if (P.ddiff == 1 && fluid_i) {"),
+    ("cubic spline inner piece", "q * q * q * 0.75);", "q * q * q * 0.5);"),
+    ("cubic spline gradient outer piece", "(t * t * -0.75) / q;", "(t * t * -0.75);"),
+    ("quadratic gradient", "* (q - T(2.0)) / q;", "* (q - T(2.0));"),
+    ("Gaussian normalisation", "- (Q / 2.0 + Q * Q * Q / 3.0) * std::exp(-Q * Q);", "- (Q / 2.0) * std::exp(-Q * Q);"),
+    ("Gaussian gradient factor", "-T(1.0 / (2.0 * kPi * h5 * gaussian_S(Q)))", "-T(1.0 / (4.0 * kPi * h5 * gaussian_S(Q)))"),
     ("viscosity switch", "if (P.visc_model == 0 && pv(udotx) < 0.0) {", "if (P.visc_model == 0 && pv(udotx) > 0.0) {"),
     ("viscosity density mean", "T rhobar = (rho[i] + rho[j]) * 0.5;", "T rhobar = (rho[i] + rho[j]);"),
     ("transposed separation", "d[a] = xi[a] - xj[a];", "d[a] = xj[a] - xi[a];"),
@@ -69,6 +88,16 @@ BATTERY = [
     lambda: ti.test_jvp_matches_central_differences_smooth(_box8()),
     ti.test_first_dt_from_initial_forces_and_cfl, ti.test_energy_non_increasing_with_artificial_viscosity,
     ti.test_predictor_corrector_second_order,
+    # model options (Table 1, Section 3)
+    *[lambda k=k, Q=Q: tm.test_kernel_unit_integral(k, Q) for k, Q in tm.KERNELS],
+    *[lambda k=k, Q=Q: tm.test_kernel_F_is_dW_dr_over_r(k, Q) for k, Q in tm.KERNELS],
+    tm.test_averaging_operators_are_the_three_means,
+    *[lambda m=m, f=f, e=e: tm.test_viscous_models_continuum_limit(0, 2.0, m, f, e)
+      for m, f, e in [(2, "stretch", 6.0), (3, "shear", 2.0), (3, "stretch", 8.0 / 3.0)]],
+    lambda: tm.test_bulk_viscosity_acts_on_divergence_only("stretch", 2.0),
+    tm.test_formulation2_conserves_momentum, tm.test_formulation2_continuity_weights_volumes,
+    tm.test_density_diffusion_laplacian, tm.test_density_diffusion_conserves_volume_weighted_mass,
+    tm.test_density_diffusion_sign_and_fluid_pairs_only,
 ]
 
 
