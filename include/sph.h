@@ -52,9 +52,36 @@ extern "C" {
 #define SPH_EBIT_TIMEOUT        4u
 #define SPH_EBIT_SKIN           8u
 
-/* viscosity models (paper Table 1 "viscous model", Section 2.1) */
+/* viscosity models (paper Table 1 "viscous model", Sections 2.1 and 3).  The laminar models
+ * use the neighbour weight omega_ij = m_j/(rho_i rho_j) and mubar_ij, the average (visc_avg)
+ * of the dynamic viscosities rho nu of i and j: */
 #define SPH_VISC_ARTIFICIAL     0  /* Monaghan artificial viscosity Pi_ij inside the pressure bracket */
-#define SPH_VISC_LAMINAR        1  /* Morris laminar term, kinematic viscosity, harmonic mean */
+#define SPH_VISC_LAMINAR        1  /* Morris: sum_j omega 2 mubar F u_ij */
+#define SPH_VISC_MORRIS         1
+#define SPH_VISC_MONAGHAN       2  /* K sum_j omega 2 mubar F (x.u/x.x) x_ij, K = 5 (3D) */
+#define SPH_VISC_ESPANOL_REVENGA 3 /* sum_j omega F ((5/3 mubar - zetabar) u_ij
+                                      + 5 (mubar/3 + zetabar)(x.u/x.x) x_ij), zeta = bulk */
+
+/* smoothing kernels (Table 1; kernel-templates listing of Section 4), 3D, normalised to
+ * unit integral; F = (1/r) dW/dr */
+#define SPH_KERNEL_WENDLAND     0  /* (2q+1)(1-q/2)^4, support 2h */
+#define SPH_KERNEL_CUBIC_SPLINE 1  /* 1 - 3/2 q^2 + 3/4 q^3 (q<1), (2-q)^3/4 (q<2) */
+#define SPH_KERNEL_QUADRATIC    2  /* (2-q)^2, support 2h */
+#define SPH_KERNEL_GAUSSIAN     3  /* exp(-q^2) - exp(-Q^2), cut at Q = kernel_radius */
+
+/* SPH formulations (Section 2.1) */
+#define SPH_FORM_1              0  /* drho_i = sum m_j u_ij.x_ij F; P_i/rho_i^2 + P_j/rho_j^2 */
+#define SPH_FORM_2              1  /* drho_i = sum (rho_i/rho_j) m_j u_ij.x_ij F; (P_i+P_j)/(rho_i rho_j) */
+
+/* averaging operator of the laminar viscosity (Table 1) */
+#define SPH_AVG_HARMONIC        0
+#define SPH_AVG_ARITHMETIC      1
+#define SPH_AVG_GEOMETRIC       2
+
+/* density diffusion (Table 1) */
+#define SPH_DDIFF_NONE          0
+#define SPH_DDIFF_MOLTENI       1  /* Molteni & Colagrossi: + 2 xi h c0 sum_j (rho_i - rho_j) F_ij m_j/rho_j
+                                      over fluid neighbours of fluid particles */
 
 /* particle types (paper Section 4, split neighbour list: fluid and boundary) */
 #define SPH_FLUID               0
@@ -91,6 +118,15 @@ typedef struct {
                                 skin/2 is reported: SPH_ERR_SKIN).  Not with sph_record. */
     uint32_t pad1;
     double   skin;           /* added to the list radius when rebuild_every > 1 (>= 0) */
+    /* model options (Table 1); all zero = Wendland C2, formulation 1, harmonic mean, no
+     * density diffusion.  Other choices run the general interaction kernels; sph_record
+     * (the adjoint) takes only the all-zero options with SPH_VISC_ARTIFICIAL or _LAMINAR. */
+    int32_t  kernel_type;    /* SPH_KERNEL_* (the Gaussian is cut at kernel_radius*h) */
+    int32_t  formulation;    /* SPH_FORM_* */
+    int32_t  visc_avg;       /* SPH_AVG_*, laminar models only */
+    int32_t  ddiff;          /* SPH_DDIFF_* */
+    double   ddiff_coef;     /* density-diffusion coefficient xi (>= 0) */
+    double   zeta;           /* kinematic bulk viscosity, SPH_VISC_ESPANOL_REVENGA (>= 0) */
 } sph_params;
 
 /* One independent scene of a batch: its own domain, grid and sound speed. */

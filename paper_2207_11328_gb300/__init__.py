@@ -43,7 +43,10 @@ class Params(ctypes.Structure):
                 ("origin", ctypes.c_double * 3), ("size", ctypes.c_double * 3),
                 ("periodic_mask", ctypes.c_uint32), ("max_particles", ctypes.c_uint32),
                 ("max_neibs", ctypes.c_uint32), ("n_scenes", ctypes.c_uint32),
-                ("rebuild_every", ctypes.c_uint32), ("pad1", ctypes.c_uint32), ("skin", ctypes.c_double)]
+                ("rebuild_every", ctypes.c_uint32), ("pad1", ctypes.c_uint32), ("skin", ctypes.c_double),
+                ("kernel_type", ctypes.c_int32), ("formulation", ctypes.c_int32),
+                ("visc_avg", ctypes.c_int32), ("ddiff", ctypes.c_int32),
+                ("ddiff_coef", ctypes.c_double), ("zeta", ctypes.c_double)]
 
 
 class SceneDesc(ctypes.Structure):
@@ -152,6 +155,9 @@ def params_from_scene(scene, max_particles=None, max_neibs=128, rebuild_every=1,
     p.n_scenes = 1
     p.rebuild_every = int(rebuild_every)
     p.skin = float(skin)
+    p.kernel_type, p.formulation = int(scene.kernel_type), int(scene.formulation)
+    p.visc_avg, p.ddiff = int(scene.visc_avg), int(scene.ddiff)
+    p.ddiff_coef, p.zeta = float(scene.ddiff_coef), float(scene.zeta)
     return p
 
 

@@ -1,6 +1,6 @@
 """Compile the CUDA library (libsph_gb300.so) for sm_103a with nvcc.
 
-Three translation units compiled in parallel, linked as a shared library
+Five translation units compiled in parallel, linked as a shared library
 with the static CUDA runtime.  Run as ``python -m paper_2207_11328_gb300._build``
 or through ``__graft_entry__.build()``.
 """
@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsph_gb300.so")
 OBJDIR = os.path.join(ROOT, "_build")
-SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "adjoint.cu"]
+SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "forces_models.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -238,8 +238,9 @@ int scene_from(const sph_params& p, const double origin[3], const double size[3]
     s.phat_coef = (float)(B / (p.rho0 * p.rho0));
     s.pi_coef = (float)(p.alpha * p.h * c0 / p.rho0);
     s.pi_unit = (float)(p.h * c0 / p.rho0);
+    s.dd_coef = (float)(2.0 * p.ddiff_coef * p.h * c0);
     double cap = p.h / c0;
-    if (p.visc_model == SPH_VISC_LAMINAR && p.nu > 0.0) cap = std::fmin(cap, p.h * p.h / p.nu);
+    if (p.visc_model != SPH_VISC_ARTIFICIAL && p.nu > 0.0) cap = std::fmin(cap, p.h * p.h / p.nu);
     s.dt_cap = p.cfl * cap;
     return SPH_OK;
 }
@@ -428,8 +429,12 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     const double gm = p->gamma;
     if (!(p->h > 0) || !(p->rho0 > 0) || !(p->c0 > 0) || !(gm >= 1 && gm <= 8 && gm == std::floor(gm)) ||
         !(p->kernel_radius > 0) || !(p->cfl > 0) || p->max_particles == 0 || p->max_particles > kMaxParticles ||
-        p->max_neibs < 8 || p->max_neibs > 1024 || (p->visc_model != SPH_VISC_ARTIFICIAL && p->visc_model != SPH_VISC_LAMINAR) ||
-        !(p->alpha >= 0) || !(p->nu >= 0) || !(p->skin >= 0) || (p->rebuild_every > 1 && !(p->skin > 0)))
+        p->max_neibs < 8 || p->max_neibs > 1024 || p->visc_model < SPH_VISC_ARTIFICIAL ||
+        p->visc_model > SPH_VISC_ESPANOL_REVENGA || !(p->alpha >= 0) || !(p->nu >= 0) || !(p->skin >= 0) ||
+        (p->rebuild_every > 1 && !(p->skin > 0)) || p->kernel_type < SPH_KERNEL_WENDLAND ||
+        p->kernel_type > SPH_KERNEL_GAUSSIAN || (p->formulation != SPH_FORM_1 && p->formulation != SPH_FORM_2) ||
+        p->visc_avg < SPH_AVG_HARMONIC || p->visc_avg > SPH_AVG_GEOMETRIC ||
+        (p->ddiff != SPH_DDIFF_NONE && p->ddiff != SPH_DDIFF_MOLTENI) || !(p->ddiff_coef >= 0) || !(p->zeta >= 0))
         return SPH_ERR_ARG;
     sph_ctx* c = new (std::nothrow) sph_ctx();
     if (!c) return SPH_ERR_ARG;
@@ -447,7 +452,21 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.skin_lim2 = (float)(0.25 * p->skin * p->skin);
     ph.skin_trig2 = (float)(0.0625 * p->skin * p->skin);
     ph.rebuild_every = p->rebuild_every;
-    ph.aF = (float)(105.0 / (128.0 * 3.14159265358979323846 * h * h * h * h * h));
+    // F = aF f(q): the unit-integral normalisations of the Table 1 kernels (3D)
+    const double pi_h5 = 3.14159265358979323846 * h * h * h * h * h;
+    switch (p->kernel_type) {
+        case SPH_KERNEL_CUBIC_SPLINE: ph.aF = (float)(1.0 / pi_h5); break;
+        case SPH_KERNEL_QUADRATIC: ph.aF = (float)(15.0 / (32.0 * pi_h5)); break;
+        case SPH_KERNEL_GAUSSIAN: {
+            // W = exp(-q^2) - exp(-Q^2) on q < Q, normalised: 4 pi h^3 aW S(Q) = 1 with
+            // S(Q) = int_0^Q (exp(-q^2) - exp(-Q^2)) q^2 dq; F = -2 aW/h^2 exp(-q^2)
+            const double Q = p->kernel_radius, eQ = std::exp(-Q * Q);
+            const double S = 0.25 * std::sqrt(3.14159265358979323846) * std::erf(Q) - 0.5 * Q * eQ - Q * Q * Q * eQ / 3.0;
+            ph.aF = (float)(1.0 / (2.0 * pi_h5 * S));
+            break;
+        }
+        default: ph.aF = (float)(105.0 / (128.0 * pi_h5)); break;
+    }
     ph.rho0 = (float)p->rho0;
     ph.inv_rho0 = (float)(1.0 / p->rho0);
     ph.eps_h2 = (float)(0.01 * h * h);
@@ -463,6 +482,24 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.cfl = p->cfl;
     ph.dt_fixed = p->dt_fixed;
     ph.visc = p->visc_model;
+    ph.kernel_type = p->kernel_type;
+    ph.form = p->formulation;
+    ph.visc_avg = p->visc_avg;
+    ph.ddiff = p->ddiff;
+    ph.general = !(p->kernel_type == SPH_KERNEL_WENDLAND && p->formulation == SPH_FORM_1 &&
+                   p->ddiff == SPH_DDIFF_NONE &&
+                   (p->visc_model == SPH_VISC_ARTIFICIAL ||
+                    (p->visc_model == SPH_VISC_MORRIS && p->visc_avg == SPH_AVG_HARMONIC)));
+    // laminar models as (lam_u u_ij + lam_x (u.x/r^2) x_ij) m_j f avg(r_i,r_j)/(r_i r_j):
+    // omega mubar = m_j nu avg/(rho0 r_i r_j), omega zetabar likewise with zeta
+    const double nu = p->nu, zeta = p->zeta, ir0 = 1.0 / p->rho0;
+    ph.lam_u = ph.lam_x = 0.f;
+    if (p->visc_model == SPH_VISC_MORRIS) ph.lam_u = (float)(2.0 * nu * ir0);
+    if (p->visc_model == SPH_VISC_MONAGHAN) ph.lam_x = (float)(10.0 * nu * ir0);
+    if (p->visc_model == SPH_VISC_ESPANOL_REVENGA) {
+        ph.lam_u = (float)((5.0 / 3.0 * nu - zeta) * ir0);
+        ph.lam_x = (float)(5.0 * (nu / 3.0 + zeta) * ir0);
+    }
     ph.max_neibs = p->max_neibs;
     ph.gamma_i = (int)gm;
     ph.build_variant = 0;
@@ -751,7 +788,8 @@ int sph_set_alpha(sph_ctx* c, double alpha) {
 int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out) {
     if (!c || T == 0 || K == 0 || T % K != 0) return SPH_ERR_ARG;
     if (!c->uploaded) return SPH_ERR_STATE;
-    if (c->g.n_scenes != 1 || skin_mode(c)) return SPH_ERR_ARG;  // one scene, list rebuilt every step
+    // one scene, list rebuilt every step, default model options
+    if (c->g.n_scenes != 1 || skin_mode(c) || c->ph.general) return SPH_ERR_ARG;
     cudaStream_t st = S(stream);
     free_tape(c);
     AdjTape& t = c->tape;

@@ -42,6 +42,7 @@ struct SceneDev {
     float phat_coef;         // B / rho0^2: P/rho^2 = phat_coef * delta*poly(delta)/(1+delta)^2
     float pi_coef;           // alpha*h*c0/rho0: Pi = -pi_coef * (u.x)/((r^2+0.01h^2)(1+(d_i+d_j)/2))
     float pi_unit;           // h*c0/rho0 (d pi_coef / d alpha)
+    float dd_coef;           // 2 xi h c0: Molteni-Colagrossi density diffusion (per-scene c0)
     double dt_cap;           // cfl * min(h/c0, h^2/nu)
 };
 
@@ -92,6 +93,13 @@ struct Phys {
     int gamma_i;             // EOS exponent (integer)
     int build_variant;       // neighbour-build kernel variant (autotuned), see build_variant_name
     int forces_variant;      // launch shape of the force kernels (autotuned), see forces_variant_name
+    // model options (Table 1); general != 0 selects the kernels of forces_models.cu
+    int general;
+    int kernel_type;         // SPH_KERNEL_*: F = aF f(q)
+    int form;                // SPH_FORM_*
+    int visc_avg;            // SPH_AVG_*
+    int ddiff;               // SPH_DDIFF_*
+    float lam_u, lam_x;      // laminar models: a += (lam_u u_ij + lam_x (u.x/r^2) x_ij) m_j f avg/(r_i r_j)
 };
 
 constexpr int kBuildVariants = 5;
@@ -202,6 +210,9 @@ enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };
 // and the corrector checks the displacement since the build.
 void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
                    int acc_dt, cudaStream_t st);
+// forces_models.cu: the same passes for the other model options of Table 1
+void launch_forces_models(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
+                          int acc_dt, cudaStream_t st);
 void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
 void launch_force_rebuild(const Buffers& b, cudaStream_t st);
 void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st);

@@ -102,6 +102,7 @@ def oracle_params_kw(scene, **kw):
     d = dict(dp=scene.dp, h=scene.h, kernel_radius=scene.kernel_radius, rho0=scene.rho0, c0=scene.c0,
              gamma=float(scene.gamma), visc_model=scene.visc, alpha=scene.alpha, nu=scene.nu, g=scene.g,
              cfl=scene.cfl, dt_fixed=scene.dt_fixed, origin=scene.origin, size=scene.size,
-             periodic_mask=scene.periodic)
+             periodic_mask=scene.periodic, kernel_type=scene.kernel_type, formulation=scene.formulation,
+             visc_avg=scene.visc_avg, ddiff=scene.ddiff, ddiff_coef=scene.ddiff_coef, zeta=scene.zeta)
     d.update(kw)
     return d
