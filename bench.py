@@ -53,11 +53,14 @@ def make_workload(name):
 
 def forces_traffic(workload):
     """Measured DRAM bytes per force launch (mean of the two passes) from the
-    committed ncu summary, or None when forces.cu changed since the capture."""
+    committed ncu summary, or None when the kernel source (forces.cu and
+    forces_common.cuh) changed since the capture."""
     import glob
     import hashlib
-    src = os.path.join(ROOT, "paper_2207_11328_gb300", "csrc", "forces.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    h = hashlib.sha256()
+    for f in ("forces.cu", "forces_common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2207_11328_gb300", "csrc", f), "rb").read())
+    sha = h.hexdigest()
     for path in glob.glob(os.path.join(ROOT, "profiles", "forces_traffic_*.md")):
         kv = {}
         for line in open(path):
@@ -67,6 +70,33 @@ def forces_traffic(workload):
         if kv.get("workload") == workload and kv.get("source_sha256") == sha:
             return 0.5 * (float(kv["predictor_dram_bytes"]) + float(kv["corrector_dram_bytes"]))
     return None
+
+
+KERNELS = {"wendland": 0, "cubic": 1, "quadratic": 2, "gaussian": 3}
+VISC = {"artificial": 0, "morris": 1, "monaghan": 2, "espanol-revenga": 3}
+
+
+def apply_physics(scene, args):
+    """Model options of Table 1 on top of the workload's own (default: the
+    workload as generated).  Returns the scene and a description."""
+    import dataclasses
+    kw = {}
+    if args.kernel != "wendland":
+        kw["kernel_type"] = KERNELS[args.kernel]
+        if args.kernel == "gaussian":
+            kw["kernel_radius"] = 3.0
+    if args.formulation == 2:
+        kw["formulation"] = 1
+    if args.visc is not None:
+        kw["visc"] = VISC[args.visc]
+        if kw["visc"] != 0:
+            kw.update(alpha=0.0, nu=args.nu)
+    if args.ddiff > 0:
+        kw.update(ddiff=1, ddiff_coef=args.ddiff)
+    desc = {"kernel": args.kernel, "formulation": args.formulation,
+            "viscosity": args.visc or ("artificial" if scene.visc == 0 else "morris"),
+            "density_diffusion": f"Molteni-Colagrossi xi={args.ddiff}" if args.ddiff > 0 else "none"}
+    return (dataclasses.replace(scene, **kw) if kw else scene), desc
 
 
 def load_peaks():
@@ -220,15 +250,62 @@ def time_oracle_steps(sub, steps, warmup=0):
     return inter, sub.n * steps, t
 
 
+_POOL_STATE = None
+
+
+def _pool_init(pkw, x, u, d, m, t):
+    global _POOL_STATE
+    import oracle
+    _POOL_STATE = (oracle.params(None, **pkw), x, u, d, m, t)
+
+
+def _pool_rhs(idx):
+    import oracle
+    p, x, u, d, m, t = _POOL_STATE
+    oracle.rhs_sample(p, x, u, d, m, t, idx)
+    return len(idx)
+
+
+def _params_kw(p):
+    return {k: (list(getattr(p, k)) if k in ("g", "origin", "size") else getattr(p, k))
+            for k, _ in p._fields_ if not k.startswith("pad")}
+
+
+def time_oracle_parallel(sub, cores, passes=2):
+    """The same oracle, unchanged, on every host core: `cores` spawned worker
+    processes each evaluate the force pass (ora_rhs_sample, neighbours
+    searched among all particles) for their share of the particles.  The
+    state is handed to the workers once, before the timed passes.
+    Returns (interactions, seconds)."""
+    import multiprocessing as mp
+    import oracle
+    p = oracle.params(sub)
+    x, u, d = sub.pos, sub.vel.astype(np.float64), sub.delta.astype(np.float64)
+    chunks = [c.astype(np.int32) for c in np.array_split(np.arange(sub.n), cores)]
+    inter = passes * interactions_of(p, sub, x)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores, initializer=_pool_init, initargs=(_params_kw(p), x, u, d, sub.mass, sub.ptype)) as pool:
+        pool.map(_pool_rhs, [c[:16] for c in chunks[:cores]])  # warm: workers started, bins code paged in
+        t0 = time.perf_counter()
+        for _ in range(passes):
+            pool.map(_pool_rhs, chunks, chunksize=1)
+        t = time.perf_counter() - t0
+    return inter, t
+
+
 def cpu_baseline(scene, workload, target_n=600_000):
     sub, w = oracle_window(scene, target_n)
     inter, psteps, t = time_oracle_steps(sub, 1)
     where = f"the corner cube x, y, z < {w:.4f} m" if w is not None else "all particles"
-    return {"value": inter / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "particle_steps_per_s": psteps / t,
-            "sample": f"1 predictor-corrector step (neighbour search + 2 force passes + dt) of the FP64 "
-                      f"oracle, single thread, on the {sub.n} particles of the workload in {where} "
-                      f"({inter} interactions, {t:.1f} s)"}
+    cores = max(1, os.cpu_count() or 1)
+    pinter, pt = time_oracle_parallel(sub, cores)
+    return {"value": pinter / pt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"2 force passes of the FP64 oracle on the {sub.n} particles of the workload in {where}, "
+                      f"split over {cores} worker processes ({pinter} interactions, {pt:.1f} s)",
+            "single_thread": {"value": inter / t, "unit": UNIT, "cores": 1, "particle_steps_per_s": psteps / t,
+                              "sample": f"1 predictor-corrector step (neighbour search + 2 force passes + dt) "
+                                        f"of the same oracle, one thread, same particles ({inter} interactions, "
+                                        f"{t:.1f} s)"}}
 
 
 def run_reference(args, world, rank):
@@ -259,12 +336,15 @@ def run_reference(args, world, rank):
 # ---------------------------------------------------------------------------
 def run_ours(args, world, rank, local):
     import torch
-    from paper_2207_11328_gb300 import Simulation, _build
+    from paper_2207_11328_gb300 import Simulation, _build, fp32_peak
 
     if rank == 0 or not os.path.exists(_build.LIB):
         _build.build()
     barrier(world)
     scene, wdesc = make_workload(args.workload)
+    scene, physics = apply_physics(scene, args)
+    if args.kernel == "gaussian":  # support 3h: ~3.4x the neighbours of 2h
+        args.max_neibs = max(args.max_neibs, 352)
     stream = torch.cuda.current_stream()
     skin_mode = args.rebuild_every > 1
     if skin_mode:  # the skin shell adds ~(1 + skin/2h)^3 - 1 of the pairs to the list
@@ -312,11 +392,19 @@ def run_ours(args, world, rank, local):
     t_corr = phases["forces_correct"] / args.profile_steps / 1e3
     achieved = (b_pred + b_corr) / (t_pred + t_corr) / 1e9
     traffic = forces_traffic(args.workload)
+    # the ALU roof: FP32 flops of a pair term (FMA = 2): separation 3, r^2 5, r 2, q - 2 2,
+    # m (q-2)^3 3, u_ij 3, u.x 5, continuity 2, pressure bracket 1, coefficient 1, a 6 = 33
+    # (+9 on approaching pairs for the artificial viscosity, not counted), per list entry
+    alu_peak = fp32_peak(stream)
+    alu = 33.0 * 2 * e_step / (t_pred + t_corr) / 1e12
     roofline = {"bound": "hbm", "kernel": "forces (predictor + corrector passes)", "achieved": achieved,
                 "peak": hbm, "peak_source": f"{peak_src} HBM copy bandwidth", "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
                 "algorithmic_bytes_per_launch": 0.5 * (b_pred + b_corr),
                 "algorithmic_bytes_per_step": b_pred + b_corr,
+                "alu": {"achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu / alu_peak,
+                        "peak_source": "measured FP32 FMA throughput (sph_fp32_peak)",
+                        "flops_per_pair": 33},
                 "phase_ms_per_step": {k: v / args.profile_steps for k, v in phases.items()}}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -324,6 +412,7 @@ def run_ours(args, world, rank, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": wdesc, "n_particles": scene.n, "n_fluid": scene.n_fluid, "dp": scene.dp,
                        "h": scene.h, "max_neibs": args.max_neibs,
+                       "physics": physics,
                        "rebuild": "every step" if not skin_mode else
                                   f"every {args.rebuild_every} steps, list radius 2h + {args.skin}h",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
@@ -475,6 +564,12 @@ def main():
     ap.add_argument("--rebuild-every", type=int, default=1,
                     help="neighbour pipeline every k steps with a skin (paper default: 10)")
     ap.add_argument("--skin", type=float, default=0.0, help="list skin in units of h (with --rebuild-every > 1)")
+    ap.add_argument("--kernel", choices=list(KERNELS), default="wendland", help="smoothing kernel (Table 1)")
+    ap.add_argument("--formulation", type=int, choices=(1, 2), default=1, help="SPH formulation (Section 2.1)")
+    ap.add_argument("--visc", choices=list(VISC), default=None, help="viscous model (default: the workload's)")
+    ap.add_argument("--nu", type=float, default=1e-6, help="kinematic viscosity of the laminar models")
+    ap.add_argument("--ddiff", type=float, default=0.0,
+                    help="Molteni-Colagrossi density-diffusion coefficient (0: off; the paper's runs use it)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -253,6 +253,12 @@ int sph_backward(sph_ctx* ctx, const float* xbar_T, const float* ubar_T, const f
  * Synchronises `stream`; SPH_ERR_STATE before an upload. */
 int sph_autotune(sph_ctx* ctx, void* stream, int* build_variant, int* forces_variant);
 
+/* Select the neighbour-build variant (0..4) and the force-kernel launch shape
+ * (0..4) directly, as sph_autotune would (-1 keeps the current one).  Every
+ * variant computes the same bits.  Synchronises the device; SPH_ERR_ARG for
+ * an index out of range. */
+int sph_set_variants(sph_ctx* ctx, int build_variant, int forces_variant);
+
 /* Names of the variants of sph_autotune (static storage). */
 const char* sph_build_variant_name(int variant);
 const char* sph_forces_variant_name(int variant);
@@ -316,6 +322,13 @@ int sph_clear_error(sph_ctx* ctx, void* stream);
 
 /* Wait for the stream and return the sticky device error (as sph_get_stats). */
 int sph_sync(sph_ctx* ctx, void* stream);
+
+/* FP32 CUDA-core throughput of the current device in TFLOP/s (FMA = 2 flops),
+ * measured with a kernel of independent FMA chains on every SM (best of 5
+ * timed launches on `stream`, synchronises it).  The ALU roof against which
+ * the interaction kernels are reported; the paper has no counterpart.
+ * Returns SPH_ERR_ARG for a null output, SPH_ERR_CUDA on a CUDA failure. */
+int sph_fp32_peak(void* stream, double* tflops);
 
 /* Human-readable text of a return code (static storage). */
 const char* sph_strerror(int code);

@@ -92,8 +92,10 @@ _SIGS = {
     "sph_set_alpha": [_vp, ctypes.c_double],
     "sph_record": [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp],
     "sph_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sph_set_variants": [_vp, ctypes.c_int, ctypes.c_int],
     "sph_build_variant_name": [ctypes.c_int],
     "sph_forces_variant_name": [ctypes.c_int],
+    "sph_fp32_peak": [_vp, _vp],
     "sph_strerror": [ctypes.c_int],
     "sph_destroy": [_vp],
 }
@@ -120,6 +122,13 @@ def _lib():
         lib.sph_destroy.restype = None
         _LIB = lib
     return _LIB
+
+
+def fp32_peak(stream=None):
+    """Measured FP32 CUDA-core throughput of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(_lib().sph_fp32_peak(_stream_handle(stream), ctypes.byref(t)), "sph_fp32_peak")
+    return t.value
 
 
 def _check(rc, where):
@@ -294,6 +303,10 @@ class Simulation:
         _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fv)),
                "sph_autotune")
         return _lib().sph_build_variant_name(v.value).decode(), _lib().sph_forces_variant_name(fv.value).decode()
+
+    def set_variants(self, build=-1, forces=-1):
+        """Select the build variant and force launch shape (0..4, -1 keeps)."""
+        _check(_lib().sph_set_variants(self._h, int(build), int(forces)), "sph_set_variants")
 
     # ---- differentiable run ---------------------------------------------------
     def set_alpha(self, alpha):

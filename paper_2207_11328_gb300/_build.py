@@ -1,6 +1,6 @@
 """Compile the CUDA library (libsph_gb300.so) for sm_103a with nvcc.
 
-Five translation units compiled in parallel, linked as a shared library
+Six translation units compiled in parallel, linked as a shared library
 with the static CUDA runtime.  Run as ``python -m paper_2207_11328_gb300._build``
 or through ``__graft_entry__.build()``.
 """
@@ -18,8 +18,13 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsph_gb300.so")
 OBJDIR = os.path.join(ROOT, "_build")
-SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "forces_models.cu", "adjoint.cu"]
+SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "forces_models.cu", "adjoint.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# The interaction kernels contract only the FMAs written as fmaf(): with the
+# compiler free to fuse a separate multiply and add, launch shapes with
+# different register caps could round differently, and every shape (and a
+# batched scene against the same scene alone) must give the same bits.
+EXTRA = {"forces.cu": ["-fmad=false"], "forces_models.cu": ["-fmad=false"]}
 
 
 def _nvcc() -> str:
@@ -35,7 +40,8 @@ def _flags(extra=()):
 
 
 def _compile(nvcc, src, obj, verbose_ptxas=False):
-    cmd = [nvcc, *(_flags(["-Xptxas", "-v"] if verbose_ptxas else [])), "-c", os.path.join(CSRC, src), "-o", obj]
+    extra = EXTRA.get(src, []) + (["-Xptxas", "-v"] if verbose_ptxas else [])
+    cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stderr}")

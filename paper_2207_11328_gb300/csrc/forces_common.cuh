@@ -2,7 +2,8 @@
 // the default model; forces_models.cu: the other model options of Table 1):
 // the central particle's shifted offsets, and the per-particle epilogue that
 // fuses the predictor or corrector update (reading C6) and the per-scene
-// max |a|^2 reduction for the CFL time step (reading C7).
+// max |a|^2 reduction for the CFL time step (reading C7).  forces.cu writes
+// the same epilogue out inline (faster there, measured).
 #pragma once
 
 #include "sph_internal.cuh"

@@ -89,7 +89,7 @@ __device__ __forceinline__ void model_pair(uint32_t e, const Central& ci, const 
     if (VISC == SPH_VISC_ARTIFICIAL) {
         if (udx < 0.f) {
             const float den = (r2 + ph.eps_h2) * fmaf(0.5f, vi.w + vj.w, 1.0f);
-            bracket -= pi_coef * __fdividef(udx, den);
+            bracket = fmaf(-pi_coef, __fdividef(udx, den), bracket);
         }
     }
     const float coef = mF * bracket;

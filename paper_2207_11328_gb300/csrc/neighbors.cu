@@ -35,9 +35,9 @@ __global__ void __launch_bounds__(kBlock) k_hash(const float4* __restrict__ pos,
         const SceneDev& sc = scenes[pinfo[i]];
         const float4 p = pos[i];
         const uint32_t c = cell[i];
-        const int sx = cell_shift(p.x, sc.inv_cell_f[0]);
-        const int sy = cell_shift(p.y, sc.inv_cell_f[1]);
-        const int sz = cell_shift(p.z, sc.inv_cell_f[2]);
+        const int sx = cell_shift(p.x, sc.cell_f[0], sc.inv_cell_f[0]);
+        const int sy = cell_shift(p.y, sc.cell_f[1], sc.inv_cell_f[1]);
+        const int sz = cell_shift(p.z, sc.cell_f[2], sc.inv_cell_f[2]);
         uint32_t k = c;
         if ((sx | sy | sz) != 0) {
             int cx, cy, cz;
@@ -234,9 +234,9 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
                 const uint32_t s = pinfo[idx];
                 const SceneDev& sc = scenes[s];
                 float4 p = pos[idx];
-                p.x -= (float)cell_shift(p.x, sc.inv_cell_f[0]) * sc.cell_f[0];
-                p.y -= (float)cell_shift(p.y, sc.inv_cell_f[1]) * sc.cell_f[1];
-                p.z -= (float)cell_shift(p.z, sc.inv_cell_f[2]) * sc.cell_f[2];
+                cell_shift(p.x, sc.cell_f[0], sc.inv_cell_f[0], &p.x);
+                cell_shift(p.y, sc.cell_f[1], sc.inv_cell_f[1], &p.y);
+                cell_shift(p.z, sc.cell_f[2], sc.inv_cell_f[2], &p.z);
                 const uint32_t d = beg + rank;
                 pos_o[d] = p;
                 vel_o[d] = vel[idx];

@@ -664,7 +664,10 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
     // all variants write the same list, so the state is unchanged by tuning
     int best_v = c->ph.build_variant;
     float best = 3.4e38f;
-    if (skin_mode(c)) launch_force_rebuild(c->b, st);  // the gated build must run while timed
+    // time the builds on a freshly sorted state: the build's candidate order relies on
+    // the in-cell sort (a skin list forces its gated pipeline open)
+    if (skin_mode(c)) launch_force_rebuild(c->b, st);
+    enqueue_build(c, st);
     for (int v = 0; v < kBuildVariants; ++v) {
         c->ph.build_variant = v;
         const float ms = time_ms([&] { launch_build(c->b, c->cur, c->g, c->ph, st); });
@@ -694,6 +697,17 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
     drop_graphs(c);  // captured launches carry the old shapes
     if (build_variant) *build_variant = best_v;
     if (forces_variant) *forces_variant = best_f;
+    return SPH_OK;
+}
+
+int sph_set_variants(sph_ctx* c, int build_variant, int forces_variant) {
+    if (!c || build_variant < -1 || build_variant >= kBuildVariants || forces_variant < -1 ||
+        forces_variant >= kForcesVariants)
+        return SPH_ERR_ARG;
+    if (build_variant >= 0) c->ph.build_variant = build_variant;
+    if (forces_variant >= 0) c->ph.forces_variant = forces_variant;
+    CK(cudaDeviceSynchronize());
+    drop_graphs(c);  // captured launches carry the old shapes
     return SPH_OK;
 }
 

@@ -119,9 +119,20 @@ __device__ __forceinline__ float eos_phat(float d, const Phys& ph, float phat_co
 }
 
 // ---- cell helpers ------------------------------------------------------
-__device__ __forceinline__ int cell_shift(float o, float inv_cell) {
-    // number of cells the offset o has moved past the cell centre
-    return (int)floorf(fmaf(o, inv_cell, 0.5f));
+__device__ __forceinline__ int cell_shift(float o, float cell, float inv_cell, float* rebased = nullptr) {
+    // number of cells the offset o has moved past the cell centre: the integer s
+    // with o - s*cell in [-cell/2, cell/2) exactly.  The estimate from o/cell can be
+    // off by one at a cell face; the exact fix-up makes re-basing idempotent (a
+    // second sort of an unchanged state moves no particle).  |s| <= 1 between sorts,
+    // where o - s*cell is exact (Sterbenz).
+    int s = (int)floorf(fmaf(o, inv_cell, 0.5f));
+    float r = o - (float)s * cell;
+    const float half = 0.5f * cell;
+    const bool up = r >= half, dn = r < -half;  // branch-free: the reorder is latency-bound
+    r = up ? r - cell : (dn ? r + cell : r);
+    s += (int)up - (int)dn;
+    if (rebased) *rebased = r;
+    return s;
 }
 
 __device__ __forceinline__ void decode_local(uint32_t local, const SceneDev& s, int& cx, int& cy, int& cz) {
