@@ -388,15 +388,23 @@ def run_ours(args, world, rank, local):
     #   forces+corrector: the same reads of the predicted state + list, read and write pos4, vel4 (64)
     b_pred = n * 72 + 4 * e_step
     b_corr = n * 104 + 4 * e_step
+    pairs_step = 2 * e_step  # pair terms evaluated by the two passes
+    if skin_mode:
+        # the predictor reads the skin list and writes the step's exact list (+ its counts),
+        # the corrector reads the exact list; pairs within 2h per pass from the counter
+        e_exact = (st2["interactions"] - st1["interactions"]) / args.profile_steps
+        b_pred = n * 76 + 4 * e_step + 4 * e_exact
+        b_corr = n * 104 + 4 * e_exact
+        pairs_step = 2 * e_exact
     t_pred = phases["forces_predict"] / args.profile_steps / 1e3
     t_corr = phases["forces_correct"] / args.profile_steps / 1e3
     achieved = (b_pred + b_corr) / (t_pred + t_corr) / 1e9
-    traffic = forces_traffic(args.workload)
+    traffic = forces_traffic(args.workload) if not skin_mode else None
     # the ALU roof: FP32 flops of a pair term (FMA = 2): separation 3, r^2 5, r 2, q - 2 2,
     # m (q-2)^3 3, u_ij 3, u.x 5, continuity 2, pressure bracket 1, coefficient 1, a 6 = 33
-    # (+9 on approaching pairs for the artificial viscosity, not counted), per list entry
+    # (+9 on approaching pairs for the artificial viscosity, not counted), per pair evaluated
     alu_peak = fp32_peak(stream)
-    alu = 33.0 * 2 * e_step / (t_pred + t_corr) / 1e12
+    alu = 33.0 * pairs_step / (t_pred + t_corr) / 1e12
     roofline = {"bound": "hbm", "kernel": "forces (predictor + corrector passes)", "achieved": achieved,
                 "peak": hbm, "peak_source": f"{peak_src} HBM copy bandwidth", "unit": "GB/s",
                 "frac": achieved / hbm, "traffic": traffic,
@@ -406,6 +414,10 @@ def run_ours(args, world, rank, local):
                         "peak_source": "measured FP32 FMA throughput (sph_fp32_peak)",
                         "flops_per_pair": 33},
                 "phase_ms_per_step": {k: v / args.profile_steps for k, v in phases.items()}}
+    if skin_mode:
+        nb = st2["builds"] - st1["builds"]
+        roofline["profiled_steps"] = {"steps": args.profile_steps, "list_builds": nb,
+                                      "build_ms_per_list_build": phases["build"] / max(1, nb)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,

@@ -347,7 +347,7 @@ void neighbors_grid(const ora_params& P, int n, const double* x, Nbrs& out) {
 /*  laminar viscous models, omega_ij = m_j/(rho_i rho_j), mubar_ij the */
 /*  average of mu = rho nu (zetabar of rho zeta):                       */
 /*    Morris    + sum_j omega 2 mubar F u_ij                             */
-/*    Monaghan  + K sum_j omega 2 mubar F (x.u/x.x) x_ij, K = 5 (C11)    */
+/*    Monaghan  + K sum_j omega 2 mubar F (x.u/x.x) x_ij, K = 5 (C14)    */
 /*    Espanol & Revenga + sum_j omega F ((5/3 mubar - zetabar) u_ij      */
 /*                         + 5 (mubar/3 + zetabar) (x.u/x.x) x_ij)       */
 /*  density diffusion, Molteni & Colagrossi (reading D1): fluid pairs  */

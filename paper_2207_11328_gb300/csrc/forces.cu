@@ -28,8 +28,8 @@ namespace {
 // One neighbour of a fluid particle.  BND: the neighbour is a boundary
 // particle (mass stored negated, velocity zero).  The kernel constant aF is
 // factored out of every term (all terms are linear in F) and applied once.
-template <int VISC, bool BND, bool SKIN>
-__device__ __forceinline__ void fluid_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i,
+template <int VISC, bool BND, bool FILTER>
+__device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i,
                                            const float4* __restrict__ pos, const float4* __restrict__ vel,
                                            const float* __restrict__ phat, float pi_coef, const Phys& ph, Acc& acc,
                                            uint32_t& npairs) {
@@ -41,9 +41,9 @@ __device__ __forceinline__ void fluid_pair(uint32_t e, const Central& ci, const 
     const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
     const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
     const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
-    if (SKIN) {
+    if (FILTER) {
         // list with a skin: pairs beyond the influence radius (F = 0) skip the arithmetic
-        if (!(r2 < ph.R2)) return;
+        if (!(r2 < ph.R2)) return false;
         ++npairs;
     }
     const float r = r2 * rsqrtf(r2);
@@ -72,17 +72,25 @@ __device__ __forceinline__ void fluid_pair(uint32_t e, const Central& ci, const 
         acc.ay = fmaf(lam, uy, acc.ay);
         acc.az = fmaf(lam, uz, acc.az);
     }
+    return true;
 }
 
-// SKIN: the list carries a skin (rebuild every k steps): skip pairs beyond the
-// cutoff, count the pairs within it (first pass), check the displacement (corrector)
+// SKIN: the list carries a skin (rebuild every k steps).  The predictor pass
+// (and sph_forces) skip pairs beyond the cutoff and count the pairs within it;
+// the predictor also writes those pairs, the step's exact list, to
+// nlist_x/ncount_x (same split layout), which the corrector pass reads as its
+// list (so both passes use the pairs within R at x^n, as with a list built
+// every step) before checking the displacement since the build.
 template <int VISC, int MODE, int kBlock, int kMinBlocks, bool SKIN>
 __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
-    int acc_dt, const float4* __restrict__ pos_ref) {
+    int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
+    uint32_t* __restrict__ ncount_x) {
+    constexpr bool FILTER = SKIN && MODE != kCorrect;
+    constexpr bool COMPACT = SKIN && MODE == kPredict;
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -95,32 +103,42 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
         const bool fluid_i = pi.w > 0.f;
         const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
         Acc acc{0.f, 0.f, 0.f, 0.f};
+        const size_t S = ph.stride;
+        uint32_t* xf = COMPACT ? nlist_x + i : nullptr;  // exact list: next fluid / boundary slot
+        uint32_t* xb = COMPACT ? nlist_x + (size_t)(ph.max_neibs - 1) * S + i : nullptr;
+        uint32_t nxf = 0, nxb = 0;
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
             const Central ci = central_of(pi, cx, cy, cz);
             // list entries come from DRAM: load four slots ahead of their use
-            const size_t S = ph.stride;
             const uint32_t* lp = nlist + i;
             uint32_t k = 0;
+// keep a pair of the exact list (COMPACT only; fluid slots upwards, boundary downwards)
+#define SPH_KEEP_F(e) if (COMPACT) { *xf = (e); xf += S; ++nxf; }
+#define SPH_KEEP_B(e) if (COMPACT) { *xb = (e); xb -= S; ++nxb; }
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
-                fluid_pair<VISC, false, SKIN>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                fluid_pair<VISC, false, SKIN>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                fluid_pair<VISC, false, SKIN>(e2, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                fluid_pair<VISC, false, SKIN>(e3, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (fluid_pair<VISC, false, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e0)
+                if (fluid_pair<VISC, false, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e1)
+                if (fluid_pair<VISC, false, FILTER>(e2, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e2)
+                if (fluid_pair<VISC, false, FILTER>(e3, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e3)
             }
-            for (; k < nf; ++k, lp += S)
-                fluid_pair<VISC, false, SKIN>(__ldg(lp), ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+            for (; k < nf; ++k, lp += S) {
+                const uint32_t e = __ldg(lp);
+                if (fluid_pair<VISC, false, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e)
+            }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             k = 0;
             for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
-                fluid_pair<VISC, true, SKIN>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                fluid_pair<VISC, true, SKIN>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (fluid_pair<VISC, true, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e0)
+                if (fluid_pair<VISC, true, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e1)
             }
-            for (; k < nb; ++k, lp -= S)
-                fluid_pair<VISC, true, SKIN>(__ldg(lp), ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+            for (; k < nb; ++k, lp -= S) {
+                const uint32_t e = __ldg(lp);
+                if (fluid_pair<VISC, true, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e)
+            }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
             acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
@@ -130,7 +148,7 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
             const Central ci = central_of(pi, cx, cy, cz);
             const uint32_t* lp = nlist + i;
 #pragma unroll 2
-            for (uint32_t k = 0; k < nf; ++k, lp += ph.stride) {
+            for (uint32_t k = 0; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
                 const uint32_t j = e >> kCodeBits;
                 const float4 pj = pos[j];
@@ -139,10 +157,11 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
                 const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
                 const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
                 const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
-                if (SKIN) {
+                if (FILTER) {
                     if (!(r2 < ph.R2)) continue;
                     ++npairs;
                 }
+                SPH_KEEP_F(e)
                 const float r = r2 * rsqrtf(r2);
                 const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
                 const float mF = pj.w * (t * t * t);
@@ -150,6 +169,15 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
                 acc.drho = fmaf(mF, udx, acc.drho);
             }
             acc.drho *= ph.aF;
+        }
+#undef SPH_KEEP_F
+#undef SPH_KEEP_B
+        if (COMPACT) {
+            if (nxf + nxb < ph.max_neibs) {
+                *xf = kMarker;
+                *xb = kMarker;
+            }
+            ncount_x[i] = nxf | (nxb << 16);
         }
 
         // epilogue written out here rather than through finish_particle() of
@@ -268,17 +296,18 @@ void launch_forces_s(const Buffers& b, int cur, const Geometry& g, const Phys& p
         case kForcesOnly:
             k_forces<VISC, kForcesOnly, B, MB, SKIN><<<grid, B, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr, nullptr, b.force, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, nullptr, nullptr, nullptr);
             break;
         case kPredict:
             k_forces<VISC, kPredict, B, MB, SKIN><<<grid, B, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s, b.phat_s, nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, nullptr, b.nlist_x, b.ncount_x);
             break;
-        case kCorrect:
+        case kCorrect:  // a skin list: the exact list the predictor wrote
             k_forces<VISC, kCorrect, B, MB, SKIN><<<grid, B, 0, st>>>(
-                b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, b.pos_ref);
+                b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur],
+                SKIN ? b.nlist_x : b.nlist, SKIN ? b.ncount_x : b.ncount, b.scenes, b.dyn, b.status, ph, 0,
+                b.pos_ref, nullptr, nullptr);
             break;
     }
 }

@@ -56,11 +56,13 @@ __device__ __forceinline__ float visc_weight(int op, float ri, float rj) {
 }
 
 // one neighbour of a fluid particle (BND: boundary neighbour, negated mass, u_j = 0)
+// (filter: skin list, skip pairs beyond the cutoff and count the rest; returns
+// whether the pair is within it)
 template <int KT, int VISC, bool BND>
-__device__ __forceinline__ void model_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i, float ri,
+__device__ __forceinline__ bool model_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i, float ri,
                                            const float4* __restrict__ pos, const float4* __restrict__ vel,
                                            const float* __restrict__ phat, float pi_coef, float dd_coef,
-                                           const Phys& ph, bool skin, Acc& acc, uint32_t& npairs) {
+                                           const Phys& ph, bool filter, Acc& acc, uint32_t& npairs) {
     const uint32_t j = e >> kCodeBits;
     const float4 pj = pos[j];
     const float4 vj = vel[j];
@@ -69,8 +71,8 @@ __device__ __forceinline__ void model_pair(uint32_t e, const Central& ci, const 
     const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
     const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
     const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
-    if (skin) {
-        if (!(r2 < ph.R2)) return;
+    if (filter) {
+        if (!(r2 < ph.R2)) return false;
         ++npairs;
     }
     const float rinv = rsqrtf(r2);
@@ -111,6 +113,7 @@ __device__ __forceinline__ void model_pair(uint32_t e, const Central& ci, const 
             acc.az = fmaf(lx, rz, acc.az);
         }
     }
+    return true;
 }
 
 template <int KT, int VISC, int MODE>
@@ -119,7 +122,12 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
-    int acc_dt, int skin, const float4* __restrict__ pos_ref) {
+    int acc_dt, int skin, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
+    uint32_t* __restrict__ ncount_x) {
+    // skin list: the predictor (and sph_forces) filter by the cutoff; the predictor keeps the
+    // pairs within it (the step's exact list) for the corrector, which reads that list as is
+    const bool filter = skin && MODE != kCorrect;
+    const bool compact = skin && MODE == kPredict;
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -134,25 +142,32 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
         const float ri = 1.0f + vi.w;
         const size_t S = ph.stride;
         Acc acc{0.f, 0.f, 0.f, 0.f};
+        uint32_t* xf = compact ? nlist_x + i : nullptr;  // exact list: next fluid / boundary slot
+        uint32_t* xb = compact ? nlist_x + (size_t)(ph.max_neibs - 1) * S + i : nullptr;
+        uint32_t nxf = 0, nxb = 0;
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef, ddc = sc.dd_coef;
             const uint32_t* lp = nlist + i;
             uint32_t k = 0;
+#define SPH_KEEP_F(e) if (compact) { *xf = (e); xf += S; ++nxf; }
+#define SPH_KEEP_B(e) if (compact) { *xb = (e); xb -= S; ++nxb; }
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
-                model_pair<KT, VISC, false>(e0, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc, npairs);
-                model_pair<KT, VISC, false>(e1, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc, npairs);
-                model_pair<KT, VISC, false>(e2, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc, npairs);
-                model_pair<KT, VISC, false>(e3, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc, npairs);
+                if (model_pair<KT, VISC, false>(e0, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e0)
+                if (model_pair<KT, VISC, false>(e1, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e1)
+                if (model_pair<KT, VISC, false>(e2, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e2)
+                if (model_pair<KT, VISC, false>(e3, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e3)
             }
-            for (; k < nf; ++k, lp += S)
-                model_pair<KT, VISC, false>(__ldg(lp), ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc,
-                                            npairs);
+            for (; k < nf; ++k, lp += S) {
+                const uint32_t e = __ldg(lp);
+                if (model_pair<KT, VISC, false>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e)
+            }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
-            for (k = 0; k < nb; ++k, lp -= S)
-                model_pair<KT, VISC, true>(__ldg(lp), ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, skin, acc,
-                                           npairs);
+            for (k = 0; k < nb; ++k, lp -= S) {
+                const uint32_t e = __ldg(lp);
+                if (model_pair<KT, VISC, true>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_B(e)
+            }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
             acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
@@ -171,10 +186,11 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
                 const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
                 const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
                 const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
-                if (skin) {
+                if (filter) {
                     if (!(r2 < ph.R2)) continue;
                     ++npairs;
                 }
+                SPH_KEEP_F(e)
                 float mF = pj.w * kernel_shape<KT>(r2, rsqrtf(r2), ph);
                 if (form2) mF *= __fdividef(ri, 1.0f + vj.w);
                 const float udx = -fmaf(vj.x, rx, fmaf(vj.y, ry, vj.z * rz));
@@ -182,10 +198,19 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             }
             acc.drho *= ph.aF;
         }
+#undef SPH_KEEP_F
+#undef SPH_KEEP_B
+        if (compact) {
+            if (nxf + nxb < ph.max_neibs) {
+                *xf = kMarker;
+                *xb = kMarker;
+            }
+            ncount_x[i] = nxf | (nxb << 16);
+        }
         finish_particle<MODE>(i, s, sc, pi, vi, fluid_i, acc, io_pos, io_vel, io_phat, force_out, dyn, st, ph,
                               acc_dt, pos_ref);
     }
-    if (skin && MODE == kPredict) {
+    if (compact) {
         const uint32_t w = __reduce_add_sync(0xffffffffu, npairs);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->interactions, (unsigned long long)w);
     }
@@ -200,17 +225,18 @@ void launch_m(const Buffers& b, int cur, const Geometry& g, const Phys& ph, Forc
         case kForcesOnly:
             k_forces_m<KT, VISC, kForcesOnly><<<grid, kModelBlock, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr, nullptr, b.force, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, skin, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, skin, nullptr, nullptr, nullptr);
             break;
         case kPredict:
             k_forces_m<KT, VISC, kPredict><<<grid, kModelBlock, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s, b.phat_s, nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin, nullptr, b.nlist_x, b.ncount_x);
             break;
         case kCorrect:
-            k_forces_m<KT, VISC, kCorrect><<<grid, kModelBlock, 0, st>>>(
-                b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin, b.pos_ref);
+            k_forces_m<KT, VISC, kCorrect><<<grid, kModelBlock, 0, st>>>(  // a skin list: the predictor's exact list
+                b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur],
+                skin ? b.nlist_x : b.nlist, skin ? b.ncount_x : b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin,
+                b.pos_ref, nullptr, nullptr);
             break;
     }
 }

@@ -528,7 +528,10 @@ int sph_create(const sph_params* p, sph_ctx** out) {
              alloc((void**)&b.cell[k], sizeof(uint32_t) * cap) && alloc((void**)&b.pinfo[k], sizeof(uint32_t) * cap) &&
              alloc((void**)&b.pid[k], sizeof(uint32_t) * cap);
     }
-    if (p->rebuild_every > 1) ok = ok && alloc((void**)&b.pos_ref, sizeof(float4) * cap);
+    if (p->rebuild_every > 1)
+        ok = ok && alloc((void**)&b.pos_ref, sizeof(float4) * cap) &&
+             alloc((void**)&b.nlist_x, sizeof(uint32_t) * (size_t)ph.stride * p->max_neibs) &&
+             alloc((void**)&b.ncount_x, sizeof(uint32_t) * cap);
     ok = ok && alloc((void**)&b.pos_s, sizeof(float4) * cap) && alloc((void**)&b.vel_s, sizeof(float4) * cap) &&
          alloc((void**)&b.phat_s, sizeof(float) * cap) &&
          alloc((void**)&b.force, sizeof(float4) * cap) && alloc((void**)&b.key, sizeof(uint32_t) * cap) &&
@@ -1176,6 +1179,8 @@ void sph_destroy(sph_ctx* c) {
         cudaFree(b.pid[k]);
     }
     cudaFree(b.pos_ref);
+    cudaFree(b.nlist_x);
+    cudaFree(b.ncount_x);
     cudaFree(b.pos_s);
     cudaFree(b.vel_s);
     cudaFree(b.phat_s);

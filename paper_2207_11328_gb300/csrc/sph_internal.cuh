@@ -156,6 +156,8 @@ struct Buffers {
     uint32_t* pid[2];
     float* phat[2];          // P/rho^2 per particle, same order as pos/vel
     float4* pos_ref;         // offsets at the last list build (rebuild_every > 1), else null
+    uint32_t* nlist_x;       // skin list: the step's exact list (pairs within R at x^n), written by
+    uint32_t* ncount_x;      //   the predictor pass, read by the corrector pass; else null
     const uint32_t* gate;    // &status->rebuild for a skin list (pipeline kernels skip when 0), else null
     float4* pos_s;           // predicted state
     float4* vel_s;
@@ -216,6 +218,8 @@ void launch_adj_store(const AdjBuffers& a, uint32_t n, float* xbar, float* ubar,
 
 // forces.cu
 enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };
+// With a skin list (pos_ref allocated) the predictor pass also writes the
+// pairs within R at x^n to nlist_x/ncount_x, and the corrector reads those.
 // With a skin list (pos_ref allocated) the kernels skip pairs beyond the
 // cutoff, the first pass counts the pairs within it (DevStatus.interactions)
 // and the corrector checks the displacement since the build.
