@@ -252,11 +252,41 @@ __global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
     }
 }
 
+// Predictor update (reading C6) from forces already stored by a
+// forces-only pass at the same state: the same operations as the predictor
+// pass's epilogue, so the result is the same to the bit.  Used by the first
+// step after a list build, whose dt0 forces pass is also its predictor's.
+__global__ void k_predict_from_forces(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                                      const float4* __restrict__ force, const uint32_t* __restrict__ pinfo,
+                                      const SceneDev* __restrict__ scenes, const SceneDyn* __restrict__ dyn,
+                                      const DevStatus* __restrict__ st, const Phys ph, float4* __restrict__ pos_o,
+                                      float4* __restrict__ vel_o, float* __restrict__ phat_o) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t s = pinfo[i];
+        const float4 pi = pos[i], vi = vel[i], a = force[i];
+        const float hd = 0.5f * dyn[s].dt;
+        float4 po = pi, vo = vi;
+        vo.w = fmaf(hd * ph.inv_rho0, a.w, vi.w);
+        if (pi.w > 0.f) {
+            vo.x = fmaf(hd, a.x, vi.x);
+            vo.y = fmaf(hd, a.y, vi.y);
+            vo.z = fmaf(hd, a.z, vi.z);
+            po.x = fmaf(hd, vi.x, pi.x);
+            po.y = fmaf(hd, vi.y, pi.y);
+            po.z = fmaf(hd, vi.z, pi.z);
+        }
+        pos_o[i] = po;
+        vel_o[i] = vo;
+        phat_o[i] = eos_phat(vo.w, ph, scenes[s].phat_coef);
+    }
+}
+
 // One thread per scene: dt for the coming step (reading C7), simulated
 // time, reset of the |a|^2 accumulator.
 __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
                      uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance, uint32_t rebuild_every,
-                     float trig2) {
+                     float trig2, uint32_t builds_inc) {
     for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
         double dt;
         if (dt_fixed > 0.0) {
@@ -283,7 +313,7 @@ __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__
             if (rb) st->maxdisp2_bits = 0u;
             st->builds += rb ? 1u : 0u;
         } else {
-            st->builds += 1u;
+            st->builds += builds_inc;
         }
     }
 }
@@ -357,9 +387,16 @@ const char* forces_variant_name(int v) {
     return v >= 0 && v < kForcesVariants ? names[v] : "?";
 }
 
-void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st) {
+void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st,
+               int with_build) {
     k_dt<<<1, 256, 0, st>>>(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, advance_time,
-                            ph.rebuild_every, ph.skin_trig2);
+                            ph.rebuild_every, ph.skin_trig2, with_build ? 1u : 0u);
+}
+
+void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    const unsigned grid = g.cap ? (g.cap + 255) / 256 : 1;
+    k_predict_from_forces<<<grid, 256, 0, st>>>(b.pos[cur], b.vel[cur], b.force, b.pinfo[cur], b.scenes, b.dyn,
+                                                b.status, ph, b.pos_s, b.vel_s, b.phat_s);
 }
 
 }  // namespace sphg

@@ -38,6 +38,7 @@ struct sph_ctx {
     uint32_t n_uploaded = 0;
     bool uploaded = false;
     bool need_dt0 = true;
+    bool fresh = false;  // the list was built for the current positions (no step since)
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step, per buffer parity
     uint32_t graph_nodes = 0;
@@ -401,6 +402,7 @@ int do_upload(sph_ctx* c, uint32_t n, const double* pos, const float* vel, const
     c->n_uploaded = n;
     c->uploaded = true;
     c->need_dt0 = true;
+    c->fresh = true;
     return SPH_OK;
 }
 
@@ -614,6 +616,7 @@ int sph_build_neighbors(sph_ctx* c, void* stream) {
     if (skin_mode(c)) launch_force_rebuild(c->b, S(stream));
     enqueue_build(c, S(stream));
     CK(cudaGetLastError());
+    c->fresh = true;
     return SPH_OK;
 }
 
@@ -629,6 +632,27 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
     if (!c) return SPH_ERR_ARG;
     if (!c->uploaded) return SPH_ERR_STATE;
     cudaStream_t st = S(stream);
+    uint32_t s = 0;
+    if (nsteps && c->fresh && !skin_mode(c)) {
+        // the list was just built for the current positions (upload, sph_build_neighbors):
+        // the first step runs without the neighbour pipeline.  Its dt0 forces pass (reading
+        // C7) is also its predictor's force evaluation: the predictor update then reads the
+        // stored forces.  Same result, to the bit, as the full step.
+        if (c->need_dt0) {
+            launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+            launch_dt(c->b, c->g, c->ph, 1, st, 0);
+            launch_predict_from_forces(c->b, c->cur, c->g, c->ph, st);
+            c->need_dt0 = false;
+        } else {
+            launch_dt(c->b, c->g, c->ph, 1, st, 0);
+            launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st);
+        }
+        launch_forces(c->b, c->cur, c->g, c->ph, kCorrect, 0, st);
+        CK(cudaGetLastError());
+        ++s;
+    }
+    c->fresh = false;
+    if (s == nsteps) return SPH_OK;
     if (c->need_dt0) {
         // dt0 from one forces call on the initial state (reading C7)
         launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
@@ -639,7 +663,7 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
         int rc = capture_graphs(c);
         if (rc) return rc;
     }
-    for (uint32_t s = 0; s < nsteps; ++s) {
+    for (; s < nsteps; ++s) {
         CK(cudaGraphLaunch(c->graph[c->cur], st));
         if (!skin_mode(c)) c->cur ^= 1;
     }
@@ -693,6 +717,7 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
         }
     }
     c->ph.forces_variant = best_f;
+    c->fresh = true;  // the last build is of the current positions
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     CK(cudaGetLastError());
@@ -875,6 +900,7 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     CK(cudaStreamSynchronize(st));
     t.valid = true;
     c->need_dt0 = true;
+    c->fresh = true;
     if (dt_out) *dt_out = dt;
     return SPH_OK;
 }
@@ -909,6 +935,7 @@ int sph_backward(sph_ctx* c, const float* xbar_T, const float* ubar_T, const flo
     state_io(c, t.ckpt[0], false, st, n);
     enqueue_build(c, st);
     c->need_dt0 = true;
+    c->fresh = true;
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(st));
     if (alphabar) *alphabar = ab;
@@ -925,6 +952,7 @@ int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_m
         launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
         c->need_dt0 = false;
     }
+    c->fresh = false;
     cudaEvent_t ev[9];
     for (auto& e : ev) CK(cudaEventCreate(&e));
     int rc = SPH_OK;

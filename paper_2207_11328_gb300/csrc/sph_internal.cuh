@@ -230,6 +230,11 @@ void launch_forces_models(const Buffers& b, int cur, const Geometry& g, const Ph
                           int acc_dt, cudaStream_t st);
 void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
 void launch_force_rebuild(const Buffers& b, cudaStream_t st);
-void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st);
+// with_build: the step runs the neighbour pipeline (counted in DevStatus.builds; a
+// skin list counts its own rebuilds)
+void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st,
+               int with_build = 1);
+// the predictor update from b.force (a forces-only pass at the same state, reading C6)
+void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 
 }  // namespace sphg

@@ -163,6 +163,23 @@ def test_every_variant_gives_the_same_bits(bv):
             assert np.array_equal(a, b), (bv, fv)
 
 
+@pytest.mark.parametrize("case", ["dam_small", "box_jitter"])
+def test_first_step_after_a_build_skips_the_pipeline_bitwise(case):
+    # the first step after an upload reuses the upload's list and its dt0 forces pass as
+    # the predictor's forces; stepping through the full pipeline instead gives the same bits
+    s = CASES[case]()
+    a = sim_for(s)
+    a.step(4)
+    b = sim_for(s)
+    b.step_profiled(1)  # kernel by kernel, the whole pipeline
+    b.step(3)
+    for x, y in zip(a.download(), b.download()):
+        assert np.array_equal(x, y)
+    sa, sb = a.stats(), b.stats()
+    assert sa["steps"] == sb["steps"] == 4 and sa["dt"] == sb["dt"]
+    assert sa["builds"] == 4 and sb["builds"] == 5  # the upload's build serves the first step of a
+
+
 def test_autotune_keeps_results_bitwise():
     # every build variant writes the same list, every block size the same sums
     s = _small_dam(dp=0.03)
