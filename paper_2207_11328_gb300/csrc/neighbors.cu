@@ -440,6 +440,126 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
 // in each cell (cell_nfluid), so a boundary particle walks only the fluid
 // part of each neighbour cell and types need no per-candidate test.
 // ---------------------------------------------------------------------
+
+// The list of particle i; returns its entry count, *nfound = pairs found
+// (more than max_neibs: overflow, the list keeps the first ones).
+__device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __restrict__ pos,
+                                                   const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
+                                                   const uint32_t* __restrict__ start,
+                                                   const uint32_t* __restrict__ cell_nfluid,
+                                                   const SceneDev* __restrict__ scenes, uint32_t* __restrict__ nlist,
+                                                   uint32_t* __restrict__ ncount, uint32_t r2lim, uint32_t max_neibs,
+                                                   uint32_t stride, uint32_t* nfound_out) {
+    constexpr int kGroup = 8;
+    const SceneDev& sc = scenes[pinfo[i]];
+    const float4 pi = pos[i];
+    const bool fluid_i = pi.w > 0.f;
+    int cx, cy, cz;
+    decode_local(cell[i] - sc.cell_offset, sc, cx, cy, cz);
+    uint32_t nfw = 0, nbw = 0, nfound = 0;
+    uint32_t* pf = nlist + i;
+    uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= sc.ncell[2]) {
+            if (!((sc.periodic >> 2) & 1u)) continue;
+            z = z < 0 ? z + sc.ncell[2] : z - sc.ncell[2];
+        }
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= sc.ncell[1]) {
+                if (!((sc.periodic >> 1) & 1u)) continue;
+                y = y < 0 ? y + sc.ncell[1] : y - sc.ncell[1];
+            }
+            const uint32_t row = sc.cell_offset + (uint32_t)sc.ncell[0] * ((uint32_t)y + (uint32_t)sc.ncell[1] * (uint32_t)z);
+            const float by = pi.y - (float)dy * sc.cell_f[1];
+            const float bz = pi.z - (float)dz * sc.cell_f[2];
+            // the row's three cell ranges, loaded together (one round trip per row)
+            uint32_t rb[3], ref[3], re[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                int x = cx + k - 1;
+                bool ok = true;
+                if (x < 0 || x >= sc.ncell[0]) {
+                    if (sc.periodic & 1u) x = x < 0 ? x + sc.ncell[0] : x - sc.ncell[0];
+                    else ok = false;
+                }
+                rb[k] = ref[k] = re[k] = 0u;
+                if (ok) {
+                    const uint32_t cc = row + (uint32_t)x;
+                    rb[k] = start[cc];
+                    ref[k] = rb[k] + cell_nfluid[cc];  // end of the fluid part
+                    re[k] = fluid_i ? start[cc + 1] : ref[k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int dx = k - 1;
+                const uint32_t b = rb[k], ef = ref[k], e = re[k];
+                const float bx = pi.x - (float)dx * sc.cell_f[0];
+                const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
+                // groups of kGroup candidates: independent loads in flight, the hits
+                // gathered in a bit mask, then appended fluid-first in candidate order
+                for (uint32_t j = b; j < e; j += kGroup) {
+                    uint32_t hits = 0;
+#pragma unroll
+                    for (int u = 0; u < kGroup; ++u) {
+                        const float4 pj = pos[min(j + u, e - 1)];
+                        const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                        // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
+                        hits |= (uint32_t)(__float_as_uint(r2) - 1u < r2lim) << u;
+                    }
+                    const uint32_t rem = e - j;
+                    if (rem < (uint32_t)kGroup) hits &= (1u << rem) - 1u;
+                    if (!hits) continue;
+                    nfound += __popc(hits);
+                    const uint32_t nfl = ef > j ? min(ef - j, (uint32_t)kGroup) : 0u;
+                    const uint32_t fm = (uint32_t)((1ull << nfl) - 1ull);
+                    uint32_t hf = hits & fm, hb = hits & ~fm;
+                    while (hf) {
+                        const int u = __ffs(hf) - 1;
+                        hf &= hf - 1u;
+                        if (nfw + nbw < max_neibs) {
+                            *pf = ((j + u) << kCodeBits) | code;
+                            pf += stride;
+                            ++nfw;
+                        }
+                    }
+                    while (hb) {
+                        const int u = __ffs(hb) - 1;
+                        hb &= hb - 1u;
+                        if (nfw + nbw < max_neibs) {
+                            *pb = ((j + u) << kCodeBits) | code;
+                            pb -= stride;
+                            ++nbw;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (nfw + nbw < max_neibs) {
+        *pf = kMarker;
+        *pb = kMarker;
+    }
+    ncount[i] = nfw | (nbw << 16);
+    *nfound_out = nfound;
+    return nfw + nbw;
+}
+
+// warp-level list statistics: overflow flag, largest count, entries written
+__device__ __forceinline__ void build_stats(DevStatus* st, uint32_t nfound, uint32_t nent, uint32_t max_neibs,
+                                            unsigned mask) {
+    if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
+    const uint32_t m = __reduce_max_sync(mask, nfound);
+    const uint32_t wsum = __reduce_add_sync(mask, nent);
+    if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1)) {
+        atomicMax(&st->max_neibs_seen, m);
+        atomicAdd(&st->list_entries, (unsigned long long)wsum);
+    }
+}
+
 template <int kBlockT>
 __global__ void __launch_bounds__(kBlockT) k_build_tpp(
     const float4* __restrict__ pos, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
@@ -447,89 +567,13 @@ __global__ void __launch_bounds__(kBlockT) k_build_tpp(
     DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,
     uint32_t max_neibs, uint32_t stride, const uint32_t* __restrict__ gate) {
     if (gate && *gate == 0u) return;  // skin list: no rebuild this step
+    const uint32_t r2lim = __float_as_uint(R2) - 1u;
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const SceneDev& sc = scenes[pinfo[i]];
-        const float4 pi = pos[i];
-        const bool fluid_i = pi.w > 0.f;
-        int cx, cy, cz;
-        decode_local(cell[i] - sc.cell_offset, sc, cx, cy, cz);
-        uint32_t nfw = 0, nbw = 0, nfound = 0;
-        uint32_t* pf = nlist + i;
-        uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;
-        for (int dz = -1; dz <= 1; ++dz) {
-            int z = cz + dz;
-            if (z < 0 || z >= sc.ncell[2]) {
-                if (!((sc.periodic >> 2) & 1u)) continue;
-                z = z < 0 ? z + sc.ncell[2] : z - sc.ncell[2];
-            }
-            for (int dy = -1; dy <= 1; ++dy) {
-                int y = cy + dy;
-                if (y < 0 || y >= sc.ncell[1]) {
-                    if (!((sc.periodic >> 1) & 1u)) continue;
-                    y = y < 0 ? y + sc.ncell[1] : y - sc.ncell[1];
-                }
-                const uint32_t row = sc.cell_offset + (uint32_t)sc.ncell[0] * ((uint32_t)y + (uint32_t)sc.ncell[1] * (uint32_t)z);
-                const float by = pi.y - (float)dy * sc.cell_f[1];
-                const float bz = pi.z - (float)dz * sc.cell_f[2];
-                for (int dx = -1; dx <= 1; ++dx) {
-                    int x = cx + dx;
-                    if (x < 0 || x >= sc.ncell[0]) {
-                        if (!(sc.periodic & 1u)) continue;
-                        x = x < 0 ? x + sc.ncell[0] : x - sc.ncell[0];
-                    }
-                    const uint32_t cc = row + (uint32_t)x;
-                    const uint32_t b = start[cc];
-                    const uint32_t ef = b + cell_nfluid[cc];             // end of the fluid part
-                    const uint32_t e = fluid_i ? start[cc + 1] : ef;
-                    const float bx = pi.x - (float)dx * sc.cell_f[0];
-                    const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
-                    // four candidates per iteration: independent loads in flight
-                    uint32_t j = b;
-                    for (; j < e; j += 4) {
-                        float r2v[4];
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const uint32_t jj = min(j + u, e - 1);
-                            const float4 pj = pos[jj];
-                            const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
-                            r2v[u] = j + u < e ? fmaf(rx, rx, fmaf(ry, ry, rz * rz)) : R2;
-                        }
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            if (r2v[u] < R2 && r2v[u] > 0.f) {
-                                ++nfound;
-                                if (nfw + nbw < max_neibs) {
-                                    const uint32_t entry = ((j + u) << kCodeBits) | code;
-                                    if (j + u < ef) {
-                                        *pf = entry;
-                                        pf += stride;
-                                        ++nfw;
-                                    } else {
-                                        *pb = entry;
-                                        pb -= stride;
-                                        ++nbw;
-                                    }
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        if (nfw + nbw < max_neibs) {
-            *pf = kMarker;
-            *pb = kMarker;
-        }
-        ncount[i] = nfw | (nbw << 16);
-        if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
-        const unsigned mask = __activemask();
-        const uint32_t m = __reduce_max_sync(mask, nfound);
-        const uint32_t wsum = __reduce_add_sync(mask, nfw + nbw);
-        if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1)) {
-            atomicMax(&st->max_neibs_seen, m);
-            atomicAdd(&st->list_entries, (unsigned long long)wsum);
-        }
+        uint32_t nfound;
+        const uint32_t nent = build_particle(i, pos, cell, pinfo, start, cell_nfluid, scenes, nlist, ncount, r2lim,
+                                             max_neibs, stride, &nfound);
+        build_stats(st, nfound, nent, max_neibs, __activemask());
     }
 }
 
