@@ -57,10 +57,9 @@ __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const 
     acc.drho = fmaf(mF, udx, acc.drho);
     float bracket = phat_i + phat_j;
     if (VISC == SPH_VISC_ARTIFICIAL) {
-        if (udx < 0.f) {
-            const float den = (r2 + ph.eps_h2) * fmaf(0.5f, vi.w + vj.w, 1.0f);
-            bracket = fmaf(-pi_coef, __fdividef(udx, den), bracket);
-        }
+        // approaching pairs only (u.x < 0), without a branch: receding pairs add -pi*0
+        const float den = (r2 + ph.eps_h2) * fmaf(0.5f, vi.w + vj.w, 1.0f);
+        bracket = fmaf(-pi_coef, __fdividef(fminf(udx, 0.f), den), bracket);
     }
     const float coef = mF * bracket;
     acc.ax = fmaf(-coef, rx, acc.ax);
