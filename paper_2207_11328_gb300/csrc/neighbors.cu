@@ -451,6 +451,7 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                                                    uint32_t* __restrict__ ncount, uint32_t r2lim, uint32_t max_neibs,
                                                    uint32_t stride, uint32_t* nfound_out) {
     constexpr int kGroup = 8;
+    static_assert(kPosPad >= kGroup - 1, "a group reads up to kGroup - 1 entries past the last particle");
     const SceneDev& sc = scenes[pinfo[i]];
     const float4 pi = pos[i];
     const bool fluid_i = pi.w > 0.f;
@@ -499,12 +500,15 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                 const float bx = pi.x - (float)dx * sc.cell_f[0];
                 const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
                 // groups of kGroup candidates: independent loads in flight, the hits
-                // gathered in a bit mask, then appended fluid-first in candidate order
+                // gathered in a bit mask, then appended fluid-first in candidate order.
+                // A group may read up to kGroup - 1 entries past the cell (the next cell's,
+                // or the kPosPad spare entries at the end): masked off below.
                 for (uint32_t j = b; j < e; j += kGroup) {
                     uint32_t hits = 0;
+                    const float4* pg = pos + j;
 #pragma unroll
                     for (int u = 0; u < kGroup; ++u) {
-                        const float4 pj = pos[min(j + u, e - 1)];
+                        const float4 pj = pg[u];
                         const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
                         const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
                         // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
@@ -561,7 +565,7 @@ __device__ __forceinline__ void build_stats(DevStatus* st, uint32_t nfound, uint
 }
 
 template <int kBlockT>
-__global__ void __launch_bounds__(kBlockT) k_build_tpp(
+__global__ void __launch_bounds__(kBlockT, 768 / kBlockT) k_build_tpp(
     const float4* __restrict__ pos, const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ start, const uint32_t* __restrict__ cell_nfluid, const SceneDev* __restrict__ scenes,
     DevStatus* __restrict__ st, uint32_t* __restrict__ nlist, uint32_t* __restrict__ ncount, float R2,

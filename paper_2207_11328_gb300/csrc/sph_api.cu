@@ -525,7 +525,9 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     auto alloc = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
-        ok = ok && alloc((void**)&b.pos[k], sizeof(float4) * cap) && alloc((void**)&b.vel[k], sizeof(float4) * cap) &&
+        // kPosPad spare entries: the build reads candidates in groups past a cell's end
+        ok = ok && alloc((void**)&b.pos[k], sizeof(float4) * (cap + kPosPad)) &&
+             alloc((void**)&b.vel[k], sizeof(float4) * cap) &&
              alloc((void**)&b.phat[k], sizeof(float) * cap) &&
              alloc((void**)&b.cell[k], sizeof(uint32_t) * cap) && alloc((void**)&b.pinfo[k], sizeof(uint32_t) * cap) &&
              alloc((void**)&b.pid[k], sizeof(uint32_t) * cap);
@@ -551,6 +553,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     cudaMemset(b.status, 0, sizeof(DevStatus));
     b.gate = p->rebuild_every > 1 ? &b.status->rebuild : nullptr;
     cudaMemset(b.force, 0, sizeof(float4) * cap);
+    for (int k = 0; k < 2; ++k) cudaMemset(b.pos[k], 0, sizeof(float4) * (cap + kPosPad));
     cudaMemset(b.ncount, 0, sizeof(uint32_t) * cap);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         sph_destroy(c);

@@ -103,6 +103,7 @@ struct Phys {
 };
 
 constexpr int kBuildVariants = 5;
+constexpr uint32_t kPosPad = 8;  // spare float4 entries after pos[k][cap - 1] (read, never used)
 const char* build_variant_name(int v);
 constexpr int kForcesVariants = 5;
 const char* forces_variant_name(int v);
