@@ -6,6 +6,8 @@ state after one full step.
   dam_break_1M : tank 1.6 x 0.67 x 0.6 m, column 0.4 x 0.67 x 0.3 m, dp 4.3 mm (1.65M particles)
   dam_break_16M: same at dp 4.3 mm / 16^(1/3)                             (~20.5M particles)
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -68,3 +70,30 @@ def test_fullsize_one_step_sampled():
     assert np.max(np.abs(dd - dd_ref)) <= 1e-4 * np.max(np.abs(dd_ref)) + 4 * np.spacing(np.float32(0.02))
     half_cell = 0.5 * max(s.size[a] / np.floor(s.size[a] / (2 * s.h)) for a in range(3))
     assert np.max(np.abs(pos - x1)) <= 1e-4 * np.max(np.abs(x1 - s.pos)) + 2 * np.spacing(np.float32(half_cell))
+
+
+def _dam_moving(dp=4.3e-3):
+    # the benchmark's dam break with a seeded velocity field and density perturbation,
+    # so that the continuity sum, the switched viscosity and the diffusion are all active
+    s = scenes.dam_break(dp=dp, name="dam_break_1M_moving")
+    f = s.ptype == 0
+    vel = s.vel.copy()
+    vel[f] = scenes.seeded_normal((int(f.sum()), 3), 0.2, 23).astype(np.float32)
+    delta = s.delta + scenes.seeded_normal((s.n,), 2e-3, 24).astype(np.float32)
+    return dataclasses.replace(s, vel=vel, delta=delta.astype(np.float32))
+
+
+@pytest.mark.parametrize("model", ["default", "density_diffusion", "all_options", "skin_list"])
+def test_fullsize_moving_state_sampled(model):
+    s = _dam_moving()
+    kw = {}
+    if model == "density_diffusion":
+        s = dataclasses.replace(s, ddiff=1, ddiff_coef=0.1)
+    elif model == "all_options":
+        s = dataclasses.replace(s, kernel_type=1, formulation=1, visc=3, visc_avg=1, alpha=0.0, nu=1e-6, zeta=1e-6,
+                                ddiff=1, ddiff_coef=0.1)
+    elif model == "skin_list":
+        kw = dict(rebuild_every=10, skin=0.3 * s.h, max_neibs=192)
+    sim = sim_for(s, **kw)
+    assert sim.stats()["error_bits"] == 0
+    _check_sample(s, sim, _sample(s.n, 3000, 12))
