@@ -24,6 +24,13 @@ struct AdjTape {
     size_t ckpt_bytes = 0, step_bytes = 0;
     sphg::AdjBuffers a{};
     void* adj_mem = nullptr;
+    // one segment of the backward pass (recompute K steps, reverse K steps) as a graph,
+    // per buffer parity at its start, and the parity it ends on
+    cudaGraphExec_t seg_graph[2] = {nullptr, nullptr};
+    int seg_end_cur[2] = {0, 0};
+    // K recorded forward steps as a graph, per buffer parity at its start
+    cudaGraphExec_t rec_graph[2] = {nullptr, nullptr};
+    int rec_end_cur[2] = {0, 0};
 };
 
 struct sph_ctx {
@@ -756,6 +763,12 @@ void free_tape(sph_ctx* c) {
     cudaFree(t.adj_mem);
     t.steps = nullptr;
     t.adj_mem = nullptr;
+    for (auto* gs : {t.seg_graph, t.rec_graph})
+        for (int k = 0; k < 2; ++k)
+            if (gs[k]) {
+                cudaGraphExecDestroy(gs[k]);
+                gs[k] = nullptr;
+            }
     t.valid = false;
 }
 
@@ -817,6 +830,24 @@ void rec_step(sph_ctx* c, const Phys& ph, char* tape_blk, int advance, cudaStrea
     launch_forces(c->b, c->cur, c->g, ph, kCorrect, 0, st);
 }
 
+// one segment of the backward pass from its checkpoint (already in buffer cur):
+// recompute the K steps forward, taping every step, then reverse through them
+// (reverse corrector -> VJP at * -> reverse predictor -> VJP at n).  No host
+// synchronisation: captured once per tape and buffer parity.
+void backward_segment(sph_ctx* c, cudaStream_t st) {
+    AdjTape& t = c->tape;
+    const uint32_t n = t.n;
+    for (uint32_t k = 0; k < t.K; ++k) rec_step(c, t.ph_rec, t.steps + (size_t)k * t.step_bytes, 0, st);
+    for (int k = (int)t.K - 1; k >= 0; --k) {
+        step_io(c, t.steps + (size_t)k * t.step_bytes, false, st, n);
+        launch_build(c->b, c->cur, c->g, t.ph_rec, st);
+        launch_adj_dphat(t.a, c->b, c->cur, c->g, t.ph_rec, st);
+        launch_adj_gather(t.a, c->b, c->cur, c->g, st);
+        launch_adj_step(t.a, c->b, c->cur, c->g, t.ph_rec, (float)t.dt, st);
+        launch_adj_scatter(t.a, c->b, c->cur, c->g, st);
+    }
+}
+
 }  // namespace
 
 int sph_set_alpha(sph_ctx* c, double alpha) {
@@ -830,34 +861,11 @@ int sph_set_alpha(sph_ctx* c, double alpha) {
     return SPH_OK;
 }
 
-int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out) {
-    if (!c || T == 0 || K == 0 || T % K != 0) return SPH_ERR_ARG;
-    if (!c->uploaded) return SPH_ERR_STATE;
-    // one scene, list rebuilt every step, default model options
-    if (c->g.n_scenes != 1 || skin_mode(c) || c->ph.general) return SPH_ERR_ARG;
-    cudaStream_t st = S(stream);
-    free_tape(c);
+namespace {
+
+int alloc_tape(sph_ctx* c) {
     AdjTape& t = c->tape;
-    DevStatus hs;
-    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const uint32_t n = hs.n_active;
-    // frozen dt: the parameter if given, else the CFL dt of one forces call on the initial state (C7)
-    double dt = c->p.dt_fixed;
-    if (!(dt > 0.0)) {
-        launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
-        launch_dt(c->b, c->g, c->ph, 0, st);
-        SceneDyn d0;
-        CK(cudaMemcpyAsync(&d0, c->b.dyn, sizeof(d0), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        dt = d0.dt_d;
-    }
-    t.T = T;
-    t.K = K;
-    t.n = n;
-    t.dt = dt;
-    t.ph_rec = c->ph;
-    t.ph_rec.dt_fixed = dt;
+    const uint32_t n = t.n, T = t.T, K = t.K;
     t.ckpt_bytes = state_bytes(n);
     t.step_bytes = step_bytes(n, c->g.n_cells);
     for (uint32_t s2 = 0; s2 < T / K; ++s2) {
@@ -887,9 +895,68 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     t.a.dphat = (float*)m; m += nf;
     t.a.dphat_s = (float*)m; m += nf;
     t.a.alpha_sum = (double*)m;
-    for (uint32_t s2 = 0; s2 < T; ++s2) {
-        if (s2 % K == 0) state_io(c, t.ckpt[s2 / K], true, st, n);
-        rec_step(c, t.ph_rec, nullptr, 1, st);
+    return SPH_OK;
+}
+
+}  // namespace
+
+int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out) {
+    if (!c || T == 0 || K == 0 || T % K != 0) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    // one scene, list rebuilt every step, default model options
+    if (c->g.n_scenes != 1 || skin_mode(c) || c->ph.general) return SPH_ERR_ARG;
+    cudaStream_t st = S(stream);
+    AdjTape& t = c->tape;
+    t.valid = false;
+    DevStatus hs;
+    CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t n = hs.n_active;
+    // frozen dt: the parameter if given, else the CFL dt of one forces call on the initial state (C7)
+    double dt = c->p.dt_fixed;
+    if (!(dt > 0.0)) {
+        launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+        launch_dt(c->b, c->g, c->ph, 0, st);
+        SceneDyn d0;
+        CK(cudaMemcpyAsync(&d0, c->b.dyn, sizeof(d0), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        dt = d0.dt_d;
+    }
+    // a tape of the same shape, dt and launch variants keeps its buffers and graphs
+    // (a training loop records and reverses the same configuration again and again)
+    const bool reuse = t.steps && t.T == T && t.K == K && t.n == n && t.dt == dt &&
+                       t.ph_rec.build_variant == c->ph.build_variant &&
+                       t.ph_rec.forces_variant == c->ph.forces_variant;
+    if (!reuse) free_tape(c);
+    t.T = T;
+    t.K = K;
+    t.n = n;
+    t.dt = dt;
+    t.ph_rec = c->ph;
+    t.ph_rec.dt_fixed = dt;
+    if (!reuse && alloc_tape(c) != SPH_OK) return SPH_ERR_CUDA;
+    // each segment: its checkpoint, then K steps (one captured graph per buffer parity)
+    int rc = SPH_OK;
+    for (uint32_t seg = 0; seg < T / K && rc == SPH_OK; ++seg) {
+        state_io(c, t.ckpt[seg], true, st, n);
+        const int p0 = c->cur;
+        if (!t.rec_graph[p0]) {
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            for (uint32_t k = 0; k < K; ++k) rec_step(c, t.ph_rec, nullptr, 1, c->cap_stream);
+            CK(cudaStreamEndCapture(c->cap_stream, &gr));
+            if (cudaGraphInstantiate(&t.rec_graph[p0], gr, 0) != cudaSuccess) rc = SPH_ERR_CUDA;
+            cudaGraphDestroy(gr);
+            t.rec_end_cur[p0] = c->cur;
+            c->cur = p0;
+        }
+        if (rc == SPH_OK && cudaGraphLaunch(t.rec_graph[p0], st) != cudaSuccess) rc = SPH_ERR_CUDA;
+        c->cur = t.rec_end_cur[p0];
+    }
+    CK(cudaStreamSynchronize(st));
+    if (rc != SPH_OK) {
+        free_tape(c);
+        return rc;
     }
     CK(cudaGetLastError());
     CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -908,6 +975,7 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     return SPH_OK;
 }
 
+
 int sph_backward(sph_ctx* c, const float* xbar_T, const float* ubar_T, const float* dbar_T, float* xbar_0,
                  float* ubar_0, float* dbar_0, double* alphabar, void* stream) {
     if (!c) return SPH_ERR_ARG;
@@ -917,18 +985,23 @@ int sph_backward(sph_ctx* c, const float* xbar_T, const float* ubar_T, const flo
     const uint32_t n = t.n;
     launch_adj_load(t.a, n, xbar_T, ubar_T, dbar_T, st);
     for (int seg = (int)(t.T / t.K) - 1; seg >= 0; --seg) {
-        // recompute the segment forward from its checkpoint, taping every step
+        // the segment's checkpoint, then its recompute and reverse (one captured graph:
+        // the same work for every segment, on the same tape buffers)
         state_io(c, t.ckpt[seg], false, st, n);
-        for (uint32_t k = 0; k < t.K; ++k) rec_step(c, t.ph_rec, t.steps + (size_t)k * t.step_bytes, 0, st);
-        // reverse through the segment
-        for (int k = (int)t.K - 1; k >= 0; --k) {
-            step_io(c, t.steps + (size_t)k * t.step_bytes, false, st, n);
-            launch_build(c->b, c->cur, c->g, t.ph_rec, st);
-            launch_adj_dphat(t.a, c->b, c->cur, c->g, t.ph_rec, st);
-            launch_adj_gather(t.a, c->b, c->cur, c->g, st);
-            launch_adj_step(t.a, c->b, c->cur, c->g, t.ph_rec, (float)t.dt, st);
-            launch_adj_scatter(t.a, c->b, c->cur, c->g, st);
+        const int p0 = c->cur;
+        if (!t.seg_graph[p0]) {
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+            backward_segment(c, c->cap_stream);
+            CK(cudaStreamEndCapture(c->cap_stream, &gr));
+            const cudaError_t e = cudaGraphInstantiate(&t.seg_graph[p0], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return SPH_ERR_CUDA;
+            t.seg_end_cur[p0] = c->cur;
+            c->cur = p0;
         }
+        CK(cudaGraphLaunch(t.seg_graph[p0], st));
+        c->cur = t.seg_end_cur[p0];
     }
     launch_adj_store(t.a, n, xbar_0, ubar_0, dbar_0, st);
     launch_adj_sum_alpha(t.a, n, t.a.alpha_sum, st);
