@@ -4,6 +4,7 @@ Each case plants one mistake in a copy of oracle/sph_oracle.cpp (a flipped
 sign, a dropped factor, a wrong coefficient or index, transposed operands, a
 wrong branch), builds it on the CPU and runs the fast pins against it: at
 least one pin must fail.  The oracle itself is never modified."""
+import concurrent.futures as cf
 import os
 import subprocess
 
@@ -83,11 +84,10 @@ BATTERY = [
     lambda: tn.test_brute_matches_numpy(7), lambda: tn.test_grid_matches_brute(7), tn.test_lattice_interior_count_is_80,
     tp.test_continuity_linear_field, tp.test_continuity_sign_approaching_pair, tp.test_pressure_gradient_linear_density,
     tp.test_mass_factor_in_pressure_term, tp.test_artificial_viscosity_switch, tp.test_laminar_shear_closed_form,
-    tp.test_boundary_particles, tp.test_cfl_dt_branches, tp.test_artificial_viscosity_shear_decay,
+    tp.test_boundary_particles, tp.test_cfl_dt_branches,
     lambda: tp.test_momentum_conserved_periodic(1, 0.0, 0.1),
     lambda: ti.test_jvp_matches_central_differences_smooth(_box8()),
-    ti.test_first_dt_from_initial_forces_and_cfl, ti.test_energy_non_increasing_with_artificial_viscosity,
-    ti.test_predictor_corrector_second_order,
+    ti.test_first_dt_from_initial_forces_and_cfl,
     # model options (Table 1, Section 3)
     *[lambda k=k, Q=Q: tm.test_kernel_unit_integral(k, Q) for k, Q in tm.KERNELS],
     *[lambda k=k, Q=Q: tm.test_kernel_F_is_dW_dr_over_r(k, Q) for k, Q in tm.KERNELS],
@@ -98,24 +98,38 @@ BATTERY = [
     tm.test_formulation2_conserves_momentum, tm.test_formulation2_continuity_weights_volumes,
     tm.test_density_diffusion_laplacian, tm.test_density_diffusion_conserves_volume_weighted_mass,
     tm.test_density_diffusion_sign_and_fluid_pairs_only,
+    # the slow pins last: most mistakes fail an earlier one
+    ti.test_energy_non_increasing_with_artificial_viscosity, tp.test_artificial_viscosity_shear_decay,
+    ti.test_predictor_corrector_second_order,
 ]
 
 
+def _compile(src_text, path):
+    src = path.with_suffix(".cpp")
+    src.write_text(src_text)
+    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+                           str(src), "-o", str(path)])
+    return str(path)
+
+
 @pytest.fixture(scope="module")
-def source():
+def libs(tmp_path_factory):
+    """Every mutant (and an unmutated copy) compiled once, in parallel."""
     with open(oracle._SRC) as f:
-        return f.read()
+        source = f.read()
+    d = tmp_path_factory.mktemp("mutants")
+    jobs = {"(unmutated)": source}
+    for name, old, new in MUTANTS:
+        assert source.count(old) >= 1, f"mutation site not found: {name}"
+        jobs[name] = source.replace(old, new, 1)
+    with cf.ThreadPoolExecutor(max(1, os.cpu_count() or 1)) as ex:
+        futs = {k: ex.submit(_compile, v, d / f"m{i}.so") for i, (k, v) in enumerate(jobs.items())}
+        return {k: f.result() for k, f in futs.items()}
 
 
 @pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_is_caught(name, old, new, source, tmp_path):
-    assert source.count(old) >= 1, f"mutation site not found: {name}"
-    src = tmp_path / "mutant.cpp"
-    src.write_text(source.replace(old, new, 1))
-    lib = tmp_path / "libmutant.so"
-    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-                           str(src), "-o", str(lib)])
-    with oracle.using(str(lib)):
+def test_planted_mistake_is_caught(name, old, new, libs):
+    with oracle.using(libs[name]):
         for pin in BATTERY:
             try:
                 pin()
@@ -124,13 +138,8 @@ def test_planted_mistake_is_caught(name, old, new, source, tmp_path):
     pytest.fail(f"planted mistake '{name}' passed every pin")
 
 
-def test_unmutated_copy_passes_the_battery(source, tmp_path):
-    src = tmp_path / "same.cpp"
-    src.write_text(source)
-    lib = tmp_path / "libsame.so"
-    subprocess.check_call(["g++", "-O1", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
-                           str(src), "-o", str(lib)])
-    with oracle.using(str(lib)):
+def test_unmutated_copy_passes_the_battery(libs):
+    with oracle.using(libs["(unmutated)"]):
         for pin in BATTERY:
             pin()
-    assert os.path.exists(lib)
+    assert os.path.exists(libs["(unmutated)"])
