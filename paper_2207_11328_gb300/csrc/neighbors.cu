@@ -450,7 +450,7 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                                                    const SceneDev* __restrict__ scenes, uint32_t* __restrict__ nlist,
                                                    uint32_t* __restrict__ ncount, uint32_t r2lim, uint32_t max_neibs,
                                                    uint32_t stride, uint32_t* nfound_out) {
-    constexpr int kGroup = 8;
+    constexpr int kGroup = 6;
     static_assert(kPosPad >= kGroup - 1, "a group reads up to kGroup - 1 entries past the last particle");
     const SceneDev& sc = scenes[pinfo[i]];
     const float4 pi = pos[i];
