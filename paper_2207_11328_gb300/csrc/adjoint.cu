@@ -251,7 +251,7 @@ __device__ __forceinline__ PairGrad pair_grad(const PairIn& p, const Phys& ph, f
 // sum_i (abar_i . a_i + drhobar_i drho_i) w.r.t. x_k, u_k, delta_k, alpha.
 // ACCUM: add to (xb, ub) instead of assigning.
 template <int VISC, bool ACCUM>
-__global__ void __launch_bounds__(kBlock) k_adj_vjp(
+__global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     const float* __restrict__ dphat, const float4* __restrict__ seed, const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount, const SceneDev* __restrict__ scenes,

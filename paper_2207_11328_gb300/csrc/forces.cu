@@ -80,8 +80,10 @@ __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const 
 // nlist_x/ncount_x (same split layout), which the corrector pass reads as its
 // list (so both passes use the pairs within R at x^n, as with a list built
 // every step) before checking the displacement since the build.
+// (the forces-only pass keeps the |a|^2 reduction for dt0 live beside the sums: it gets
+// a looser register cap than the step's passes, so that no shape spills)
 template <int VISC, int MODE, int kBlock, int kMinBlocks, bool SKIN>
-__global__ void __launch_bounds__(kBlock, kMinBlocks) k_forces(
+__global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 + 2) / 3 : kMinBlocks) k_forces(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,

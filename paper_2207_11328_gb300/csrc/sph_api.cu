@@ -720,7 +720,8 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
     best = 3.4e38f;
     for (int v = 0; v < kForcesVariants; ++v) {
         c->ph.forces_variant = v;
-        const float ms = time_ms([&] { launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, st); });
+        // the predictor pass as the step runs it (it writes only the predicted-state scratch)
+        const float ms = time_ms([&] { launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st); });
         if (ms < best) {
             best = ms;
             best_f = v;
