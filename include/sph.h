@@ -309,6 +309,16 @@ int sph_download_neighbors(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t*
  * sph_download_neighbors; synchronises `stream`. */
 int sph_download_neighbors_noalloc(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream);
 
+/* Conservation sums at the current state (paper Section 2.1 invariants), from one
+ * forces-only pass (its results also land where sph_download_forces reads them):
+ *   out[0..2] momentum sum_i m_i u_i (fluid),  out[3..5] force sum_i m_i a_i,
+ *   out[6] sum_i m_i drho_i/dt,  out[7] kinetic energy sum_i m_i |u_i|^2 / 2,
+ * masses taken positive.  With no boundary particles and no gravity the pair forces
+ * cancel: out[3..5] vanish to rounding.  FP64 sums in a fixed order (bitwise
+ * reproducible).  HOST out[8]; synchronises `stream`; returns the sticky device
+ * error as sph_get_stats does. */
+int sph_conservation(sph_ctx* ctx, double* out, void* stream);
+
 /* Read device counters into *out (synchronises `stream`).  Returns the
  * sticky device error as a code (SPH_ERR_NEIB_OVERFLOW, SPH_ERR_NONFINITE,
  * SPH_ERR_TIMEOUT) if one is set, else SPH_OK; *out is filled either way. */

@@ -96,6 +96,7 @@ _SIGS = {
     "sph_build_variant_name": [ctypes.c_int],
     "sph_forces_variant_name": [ctypes.c_int],
     "sph_fp32_peak": [_vp, _vp],
+    "sph_conservation": [_vp, _vp, _vp],
     "sph_strerror": [ctypes.c_int],
     "sph_destroy": [_vp],
 }
@@ -303,6 +304,12 @@ class Simulation:
         _check(_lib().sph_autotune(self._h, _stream_handle(stream), ctypes.byref(v), ctypes.byref(fv)),
                "sph_autotune")
         return _lib().sph_build_variant_name(v.value).decode(), _lib().sph_forces_variant_name(fv.value).decode()
+
+    def conservation(self, stream=None):
+        """Momentum (3), force sum m a (3), sum m drho/dt, kinetic energy at the current state."""
+        out = np.zeros(8, np.float64)
+        _check(_lib().sph_conservation(self._h, _ptr(out), _stream_handle(stream)), "sph_conservation")
+        return {"momentum": out[0:3], "force": out[3:6], "mass_rate": out[6], "kinetic": out[7]}
 
     def set_variants(self, build=-1, forces=-1):
         """Select the build variant and force launch shape (0..4, -1 keeps)."""

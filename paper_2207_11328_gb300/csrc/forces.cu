@@ -366,7 +366,62 @@ void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& p
     }
 }
 
+// Conservation sums (Section 2.1 invariants) over particles: momentum sum m u,
+// force sum m a, sum m drho/dt, kinetic energy; |m| (boundary masses are stored
+// negated).  Deterministic: a fixed grid, a fixed particle order per thread and
+// fixed-order tree reductions in FP64 (per block, then over blocks).
+constexpr int kConsBlocks = 304, kConsThreads = 256, kConsQ = 8;
+
+__global__ void __launch_bounds__(kConsThreads) k_cons_partial(const float4* __restrict__ pos,
+                                                               const float4* __restrict__ vel,
+                                                               const float4* __restrict__ force,
+                                                               const DevStatus* __restrict__ st,
+                                                               double* __restrict__ part) {
+    __shared__ double red[kConsQ][kConsThreads];
+    double q[kConsQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * kConsThreads + threadIdx.x; i < n; i += kConsBlocks * kConsThreads) {
+        const double m = fabs((double)pos[i].w);
+        const float4 v = vel[i], a = force[i];
+        const bool fluid = pos[i].w > 0.f;
+        const double ux = fluid ? v.x : 0.0, uy = fluid ? v.y : 0.0, uz = fluid ? v.z : 0.0;
+        q[0] += m * ux;
+        q[1] += m * uy;
+        q[2] += m * uz;
+        q[3] += m * a.x;
+        q[4] += m * a.y;
+        q[5] += m * a.z;
+        q[6] += m * a.w;
+        q[7] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+    }
+#pragma unroll
+    for (int k = 0; k < kConsQ; ++k) red[k][threadIdx.x] = q[k];
+    __syncthreads();
+    for (int w = kConsThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int k = 0; k < kConsQ; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < kConsQ) part[blockIdx.x * kConsQ + threadIdx.x] = red[threadIdx.x][0];
+}
+
+__global__ void k_cons_final(const double* __restrict__ part, double* __restrict__ out) {
+    if (threadIdx.x < kConsQ) {
+        double s = 0.0;
+        for (int b = 0; b < kConsBlocks; ++b) s += part[b * kConsQ + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
 }  // namespace
+
+size_t conservation_scratch_bytes() { return sizeof(double) * kConsQ * (kConsBlocks + 1); }
+
+void launch_conservation(const Buffers& b, int cur, double* scratch, cudaStream_t st) {
+    k_cons_partial<<<kConsBlocks, kConsThreads, 0, st>>>(b.pos[cur], b.vel[cur], b.force, b.status, scratch);
+    k_cons_final<<<1, 32, 0, st>>>(scratch, scratch + kConsQ * kConsBlocks);
+}
 
 void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
                    cudaStream_t st) {

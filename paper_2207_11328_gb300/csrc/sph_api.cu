@@ -549,7 +549,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
          alloc((void**)&b.slot, sizeof(uint32_t) * cap) && alloc((void**)&b.unsorted, sizeof(uint32_t) * cap) &&
          alloc((void**)&b.nlist, sizeof(uint32_t) * (size_t)ph.stride * p->max_neibs) &&
          alloc((void**)&b.ncount, sizeof(uint32_t) * cap) && alloc((void**)&b.status, sizeof(DevStatus));
-    c->staging_bytes = 64 * (size_t)cap + 4096;
+    c->staging_bytes = 64 * (size_t)cap + 32768;  // >= the conservation sums' scratch
     ok = ok && alloc(&b.staging, c->staging_bytes);
     ok = ok && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (!ok) {
@@ -628,6 +628,23 @@ int sph_build_neighbors(sph_ctx* c, void* stream) {
     CK(cudaGetLastError());
     c->fresh = true;
     return SPH_OK;
+}
+
+int sph_conservation(sph_ctx* c, double* out, void* stream) {
+    if (!c || !out) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    const size_t bytes = conservation_scratch_bytes();
+    if (bytes > c->staging_bytes) return SPH_ERR_CAPACITY;
+    double* scratch = (double*)c->b.staging;
+    launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, st);
+    launch_conservation(c->b, c->cur, scratch, st);
+    CK(cudaMemcpyAsync(out, (char*)scratch + bytes - 8 * sizeof(double), 8 * sizeof(double), cudaMemcpyDeviceToHost,
+                       st));
+    CK(cudaStreamSynchronize(st));
+    DevStatus hs;
+    CK(cudaMemcpy(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost));
+    return error_from_bits(hs.error_bits);
 }
 
 int sph_forces(sph_ctx* c, void* stream) {

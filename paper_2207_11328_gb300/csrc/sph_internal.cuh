@@ -230,6 +230,10 @@ void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph,
 void launch_forces_models(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
                           int acc_dt, cudaStream_t st);
 void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+// conservation sums of the state in buffer cur and the forces in b.force (8 doubles at
+// scratch + 8 * 304, after 304 * 8 doubles of block partials)
+size_t conservation_scratch_bytes();
+void launch_conservation(const Buffers& b, int cur, double* scratch, cudaStream_t st);
 void launch_force_rebuild(const Buffers& b, cudaStream_t st);
 // with_build: the step runs the neighbour pipeline (counted in DevStatus.builds; a
 // skin list counts its own rebuilds)
