@@ -45,12 +45,15 @@ extern "C" {
 #define SPH_ERR_TIMEOUT        -7  /* a bounded device wait gave up */
 #define SPH_ERR_STATE          -8  /* call out of order (e.g. step before upload) */
 #define SPH_ERR_SKIN           -9  /* a particle moved more than skin/2 since the last list build */
+#define SPH_ERR_BOUNDS        -10  /* checked build only: an index out of range or a buffer's canary tail
+                                      overwritten (the access was skipped) */
 
 /* device error word bits (sph_stats.error_bits) */
 #define SPH_EBIT_NEIB_OVERFLOW  1u
 #define SPH_EBIT_NONFINITE      2u
 #define SPH_EBIT_TIMEOUT        4u
 #define SPH_EBIT_SKIN           8u
+#define SPH_EBIT_BOUNDS        16u  /* checked build (compiled with SPH_CHECKED) */
 
 /* viscosity models (paper Table 1 "viscous model", Sections 2.1 and 3).  The laminar models
  * use the neighbour weight omega_ij = m_j/(rho_i rho_j) and mubar_ij, the average (visc_avg)

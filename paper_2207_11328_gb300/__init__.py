@@ -20,12 +20,15 @@ import numpy as np
 from . import scenes  # noqa: F401  (seeded generators; no method arithmetic)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsph_gb300.so")
+# SPH_GB300_CHECKED=1 loads the checked build (bounds checks and buffer canaries that
+# report SPH_ERR_BOUNDS instead of faulting); set it before the first call.
+LIB_PATH = os.path.join(_HERE, "libsph_gb300_checked.so" if os.environ.get("SPH_GB300_CHECKED") == "1"
+                        else "libsph_gb300.so")
 
 SPH_OK = 0
 _ERRNAMES = {-1: "SPH_ERR_ARG", -2: "SPH_ERR_CUDA", -3: "SPH_ERR_CAPACITY", -4: "SPH_ERR_NEIB_OVERFLOW",
              -5: "SPH_ERR_OUT_OF_DOMAIN", -6: "SPH_ERR_NONFINITE", -7: "SPH_ERR_TIMEOUT", -8: "SPH_ERR_STATE",
-             -9: "SPH_ERR_SKIN"}
+             -9: "SPH_ERR_SKIN", -10: "SPH_ERR_BOUNDS"}
 
 
 class SphError(RuntimeError):

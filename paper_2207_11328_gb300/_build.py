@@ -17,6 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libsph_gb300.so")
+LIB_CHECKED = os.path.join(HERE, "libsph_gb300_checked.so")  # -DSPH_CHECKED: bounds checks, canaries
 OBJDIR = os.path.join(ROOT, "_build")
 SOURCES = ["sph_api.cu", "neighbors.cu", "forces.cu", "forces_models.cu", "adjoint.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,8 +40,8 @@ def _flags(extra=()):
                    *extra]
 
 
-def _compile(nvcc, src, obj, verbose_ptxas=False):
-    extra = EXTRA.get(src, []) + (["-Xptxas", "-v"] if verbose_ptxas else [])
+def _compile(nvcc, src, obj, verbose_ptxas=False, checked=False):
+    extra = EXTRA.get(src, []) + (["-Xptxas", "-v"] if verbose_ptxas else []) + (["-DSPH_CHECKED"] if checked else [])
     cmd = [nvcc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -48,32 +49,41 @@ def _compile(nvcc, src, obj, verbose_ptxas=False):
     return r.stderr
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib=LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "sph.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
+def build(force: bool = False, verbose_ptxas: bool = False, checked: bool = False) -> str:
+    """Build the library (checked=True: the variant compiled with SPH_CHECKED)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and not _stale(lib):
+        return lib
     nvcc = _nvcc()
-    os.makedirs(OBJDIR, exist_ok=True)
-    objs = [os.path.join(OBJDIR, s.replace(".cu", ".o")) for s in SOURCES]
+    objdir = os.path.join(OBJDIR, "checked") if checked else OBJDIR
+    os.makedirs(objdir, exist_ok=True)
+    objs = [os.path.join(objdir, s.replace(".cu", ".o")) for s in SOURCES]
     with cf.ThreadPoolExecutor(len(SOURCES)) as ex:
-        logs = list(ex.map(lambda a: _compile(nvcc, a[0], a[1], verbose_ptxas), zip(SOURCES, objs)))
+        logs = list(ex.map(lambda a: _compile(nvcc, a[0], a[1], verbose_ptxas, checked), zip(SOURCES, objs)))
     if verbose_ptxas:
         for s, log in zip(SOURCES, logs):
             sys.stderr.write(f"== {s}\n{log}")
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build_all(force: bool = False) -> list:
+    """Both libraries, compiled concurrently."""
+    with cf.ThreadPoolExecutor(2) as ex:
+        return list(ex.map(lambda c: build(force=force, checked=c), (False, True)))
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv))
+    print(build(force="--force" in sys.argv, verbose_ptxas="-v" in sys.argv, checked="--checked" in sys.argv))

@@ -271,6 +271,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
             const uint32_t slot = q < nf ? q : ph.max_neibs - 1 - (q - nf);
             const uint32_t e = nlist[(size_t)slot * ph.stride + k];
             const uint32_t j = e >> kCodeBits;
+            SPH_GUARD(j < st->n_active, st, continue)
             const float4 pj = pos[j];
             const float4 vj = vel[j];
             const float4 sj = seed[j];

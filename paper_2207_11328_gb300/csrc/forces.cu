@@ -100,7 +100,8 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
         const float4 pi = pos[i];
         const float4 vi = vel[i];
         const uint32_t cnt = ncount[i];
-        const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        SPH_GUARD(nf + nb <= ph.max_neibs, st, nf = nb = 0)
         const bool fluid_i = pi.w > 0.f;
         const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
         Acc acc{0.f, 0.f, 0.f, 0.f};
@@ -120,6 +121,7 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
 #define SPH_KEEP_B(e) if (COMPACT) { *xb = (e); xb -= S; ++nxb; }
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
+                SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
                 if (fluid_pair<VISC, false, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e0)
                 if (fluid_pair<VISC, false, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e1)
                 if (fluid_pair<VISC, false, FILTER>(e2, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e2)
@@ -127,17 +129,20 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             }
             for (; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
+                SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (fluid_pair<VISC, false, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e)
             }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             k = 0;
             for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
+                SPH_GUARD((max(e0, e1) >> kCodeBits) < n, st, break)
                 if (fluid_pair<VISC, true, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e0)
                 if (fluid_pair<VISC, true, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e1)
             }
             for (; k < nb; ++k, lp -= S) {
                 const uint32_t e = __ldg(lp);
+                SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (fluid_pair<VISC, true, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e)
             }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
@@ -152,6 +157,7 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             for (uint32_t k = 0; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
                 const uint32_t j = e >> kCodeBits;
+                SPH_GUARD(j < n, st, continue)
                 const float4 pj = pos[j];
                 const float4 vj = vel[j];
                 const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;

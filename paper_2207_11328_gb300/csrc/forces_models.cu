@@ -135,7 +135,8 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
         const float4 pi = pos[i];
         const float4 vi = vel[i];
         const uint32_t cnt = ncount[i];
-        const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        SPH_GUARD(nf + nb <= ph.max_neibs, st, nf = nb = 0)
         const bool fluid_i = pi.w > 0.f;
         const Central ci = central_of(pi, sc.cell_f[0], sc.cell_f[1], sc.cell_f[2]);
         const float ri = 1.0f + vi.w;
@@ -153,6 +154,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
 #define SPH_KEEP_B(e) if (compact) { *xb = (e); xb -= S; ++nxb; }
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
+                SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
                 if (model_pair<KT, VISC, false>(e0, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e0)
                 if (model_pair<KT, VISC, false>(e1, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e1)
                 if (model_pair<KT, VISC, false>(e2, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e2)
@@ -160,11 +162,13 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             }
             for (; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
+                SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, false>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e)
             }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             for (k = 0; k < nb; ++k, lp -= S) {
                 const uint32_t e = __ldg(lp);
+                SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, true>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_B(e)
             }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
@@ -179,6 +183,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             for (uint32_t k = 0; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
                 const uint32_t j = e >> kCodeBits;
+                SPH_GUARD(j < n, st, continue)
                 const float4 pj = pos[j];
                 const float4 vj = vel[j];
                 const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;

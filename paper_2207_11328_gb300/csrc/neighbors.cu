@@ -171,11 +171,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(uint32_t* __restrict
 __global__ void __launch_bounds__(kBlock) k_scatter(const uint32_t* __restrict__ key, const uint32_t* __restrict__ slot,
                                                     const uint32_t* __restrict__ start,
                                                     const DevStatus* __restrict__ st, uint32_t* __restrict__ unsorted,
-                                                    const uint32_t* __restrict__ gate) {
+                                                    uint32_t nkeys, const uint32_t* __restrict__ gate) {
     if (gate && *gate == 0u) return;  // skin list: no rebuild this step
     const uint32_t n = st->n_active;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+    (void)nkeys;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        SPH_GUARD(key[i] < nkeys && start[key[i]] + slot[i] < start[key[i] + 1], st, continue)
         unsorted[start[key[i]] + slot[i]] = i;
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -238,6 +241,7 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
                 cell_shift(p.y, sc.cell_f[1], sc.inv_cell_f[1], &p.y);
                 cell_shift(p.z, sc.cell_f[2], sc.inv_cell_f[2], &p.z);
                 const uint32_t d = beg + rank;
+                SPH_GUARD(d < end, st, continue)
                 pos_o[d] = p;
                 vel_o[d] = vel[idx];
                 phat_o[d] = phat[idx];
@@ -353,6 +357,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
                     const uint32_t t1 = min(n, w1 - off);
                     for (uint32_t t = t0 + lane; t < t1; t += 32) {
                         const uint32_t j = b + t;
+                        SPH_GUARD(j < st->n_active, st, continue)
                         float4 q = pos[j];
                         q.x += shx;
                         q.y += shy;
@@ -449,7 +454,7 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                                                    const uint32_t* __restrict__ cell_nfluid,
                                                    const SceneDev* __restrict__ scenes, uint32_t* __restrict__ nlist,
                                                    uint32_t* __restrict__ ncount, uint32_t r2lim, uint32_t max_neibs,
-                                                   uint32_t stride, uint32_t* nfound_out) {
+                                                   uint32_t stride, uint32_t* nfound_out, DevStatus* st, uint32_t n) {
     constexpr int kGroup = 6;
     static_assert(kPosPad >= kGroup - 1, "a group reads up to kGroup - 1 entries past the last particle");
     const SceneDev& sc = scenes[pinfo[i]];
@@ -491,6 +496,8 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                     rb[k] = start[cc];
                     ref[k] = rb[k] + cell_nfluid[cc];  // end of the fluid part
                     re[k] = fluid_i ? start[cc + 1] : ref[k];
+                    SPH_GUARD(rb[k] <= ref[k] && ref[k] <= start[cc + 1] && start[cc + 1] <= n, st,
+                              rb[k] = ref[k] = re[k] = 0u)
                 }
             }
 #pragma unroll
@@ -576,7 +583,7 @@ __global__ void __launch_bounds__(kBlockT, 768 / kBlockT) k_build_tpp(
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         uint32_t nfound;
         const uint32_t nent = build_particle(i, pos, cell, pinfo, start, cell_nfluid, scenes, nlist, ncount, r2lim,
-                                             max_neibs, stride, &nfound);
+                                             max_neibs, stride, &nfound, st, n);
         build_stats(st, nfound, nent, max_neibs, __activemask());
     }
 }
@@ -606,7 +613,8 @@ void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st) {
 
 void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
     (void)cur;
-    k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted, b.gate);
+    k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted,
+                                                           g.n_cells + 1, b.gate);
 }
 
 void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {

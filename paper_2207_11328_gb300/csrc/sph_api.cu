@@ -50,9 +50,46 @@ struct sph_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step, per buffer parity
     uint32_t graph_nodes = 0;
     size_t staging_bytes = 0;
+    std::vector<std::pair<char*, size_t>> canaries;  // checked build: (base, bytes) of guarded buffers
 };
 
 namespace {
+
+// Device allocation.  The checked build (SPH_CHECKED) adds a 256-byte canary
+// tail to each buffer, filled with 0xA5 and verified whenever the device
+// counters are read; a changed byte records SPH_EBIT_BOUNDS.
+#ifdef SPH_CHECKED
+constexpr size_t kCanary = 256;
+#else
+constexpr size_t kCanary = 0;
+#endif
+
+cudaError_t dev_alloc(sph_ctx* c, void** ptr, size_t bytes) {
+    if (!bytes) bytes = 16;
+    cudaError_t e = cudaMalloc(ptr, bytes + kCanary);
+    if (e != cudaSuccess || !kCanary) return e;
+    e = cudaMemset((char*)*ptr + bytes, 0xA5, kCanary);
+    c->canaries.push_back({(char*)*ptr, bytes});
+    return e;
+}
+
+void drop_canary(sph_ctx* c, const void* base) {
+    for (size_t k = 0; k < c->canaries.size(); ++k)
+        if (c->canaries[k].first == base) {
+            c->canaries.erase(c->canaries.begin() + (long)k);
+            return;
+        }
+}
+
+__global__ void k_check_canary(const uint8_t* __restrict__ tail, uint32_t bytes, sphg::DevStatus* st) {
+    for (uint32_t k = threadIdx.x; k < bytes; k += blockDim.x)
+        if (tail[k] != 0xA5u) atomicOr(&st->error_bits, SPH_EBIT_BOUNDS);
+}
+
+void check_canaries(sph_ctx* c, cudaStream_t st) {
+    for (auto& cb : c->canaries)
+        k_check_canary<<<1, 256, 0, st>>>((const uint8_t*)cb.first + cb.second, (uint32_t)kCanary, c->b.status);
+}
 
 #define CK(call)                                                        \
     do {                                                                \
@@ -254,6 +291,9 @@ int scene_from(const sph_params& p, const double origin[3], const double size[3]
 }
 
 void free_cells(sph_ctx* c) {
+    for (const void* q : {(const void*)c->b.count, (const void*)c->b.start, (const void*)c->b.bsum,
+                          (const void*)c->b.cell_nfluid})
+        drop_canary(c, q);
     cudaFree(c->b.count);
     cudaFree(c->b.start);
     cudaFree(c->b.bsum);
@@ -277,12 +317,12 @@ inline bool skin_mode(const sph_ctx* c) { return c->p.rebuild_every > 1; }
 
 int alloc_cells(sph_ctx* c) {
     const uint32_t nb = c->g.n_cells + 1;
-    CK(cudaMalloc(&c->b.count, sizeof(uint32_t) * nb));
+    CK(dev_alloc(c, (void**)&c->b.count, sizeof(uint32_t) * nb));
     CK(cudaMemset(c->b.count, 0, sizeof(uint32_t) * nb));
-    CK(cudaMalloc(&c->b.start, sizeof(uint32_t) * (nb + 1)));
+    CK(dev_alloc(c, (void**)&c->b.start, sizeof(uint32_t) * (nb + 1)));
     CK(cudaMemset(c->b.start, 0, sizeof(uint32_t) * (nb + 1)));
-    CK(cudaMalloc(&c->b.bsum, sizeof(uint32_t) * (scan_blocks(nb) + 1)));
-    CK(cudaMalloc(&c->b.cell_nfluid, sizeof(uint32_t) * nb));
+    CK(dev_alloc(c, (void**)&c->b.bsum, sizeof(uint32_t) * (scan_blocks(nb) + 1)));
+    CK(dev_alloc(c, (void**)&c->b.cell_nfluid, sizeof(uint32_t) * nb));
     CK(cudaMemset(c->b.cell_nfluid, 0, sizeof(uint32_t) * nb));
     CK(cudaMalloc(&c->b.scenes, sizeof(SceneDev) * c->g.n_scenes));
     CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->g.n_scenes, cudaMemcpyHostToDevice));
@@ -373,6 +413,7 @@ int error_from_bits(uint32_t bits) {
     if (bits & SPH_EBIT_NEIB_OVERFLOW) return SPH_ERR_NEIB_OVERFLOW;
     if (bits & SPH_EBIT_NONFINITE) return SPH_ERR_NONFINITE;
     if (bits & SPH_EBIT_SKIN) return SPH_ERR_SKIN;
+    if (bits & SPH_EBIT_BOUNDS) return SPH_ERR_BOUNDS;
     if (bits & SPH_EBIT_TIMEOUT) return SPH_ERR_TIMEOUT;
     return SPH_OK;
 }
@@ -429,6 +470,7 @@ const char* sph_strerror(int code) {
         case SPH_ERR_TIMEOUT: return "device wait timed out";
         case SPH_ERR_STATE: return "call out of order";
         case SPH_ERR_SKIN: return "a particle moved more than skin/2 since the last neighbour-list build";
+        case SPH_ERR_BOUNDS: return "index out of range or buffer tail overwritten (checked build)";
         default: return "unknown error";
     }
 }
@@ -529,7 +571,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
         return rc;
     }
     Buffers& b = c->b;
-    auto alloc = [&](void** ptr, size_t bytes) -> bool { return cudaMalloc(ptr, bytes ? bytes : 16) == cudaSuccess; };
+    auto alloc = [&](void** ptr, size_t bytes) -> bool { return dev_alloc(c, ptr, bytes) == cudaSuccess; };
     bool ok = true;
     for (int k = 0; k < 2; ++k) {
         // kPosPad spare entries: the build reads candidates in groups past a cell's end
@@ -1240,6 +1282,7 @@ int sph_download_neighbors_noalloc(sph_ctx* c, uint32_t n, uint32_t* counts, uin
 int sph_get_stats(sph_ctx* c, sph_stats* out, void* stream) {
     if (!c || !out) return SPH_ERR_ARG;
     cudaStream_t st = S(stream);
+    if (kCanary) check_canaries(c, st);
     DevStatus hs;
     SceneDyn d0;
     CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));

@@ -119,6 +119,21 @@ __device__ __forceinline__ float eos_phat(float d, const Phys& ph, float phat_co
     return phat_coef * d * poly / (opd * opd);
 }
 
+// ---- checked build ----------------------------------------------------
+// Compiled with SPH_CHECKED, the kernels test the list and cell indices they
+// follow; a bad one records SPH_EBIT_BOUNDS and the access is skipped (no trap).
+// The ordinary build compiles the checks away.
+#ifdef SPH_CHECKED
+#define SPH_GUARD(cond, st, action)                                                   \
+    if (!(cond)) {                                                                    \
+        atomicOr(&const_cast<DevStatus*>(static_cast<const DevStatus*>(st))->error_bits, \
+                 SPH_EBIT_BOUNDS);                                                    \
+        action;                                                                       \
+    }
+#else
+#define SPH_GUARD(cond, st, action)
+#endif
+
 // ---- cell helpers ------------------------------------------------------
 __device__ __forceinline__ int cell_shift(float o, float cell, float inv_cell, float* rebased = nullptr) {
     // number of cells the offset o has moved past the cell centre: the integer s

@@ -55,3 +55,13 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(sph, "_LIB", None)
     with pytest.raises(ImportError):
         sph._lib()
+
+
+def test_checked_library_exports_the_same_boundary():
+    # the variant compiled with SPH_CHECKED (bounds checks, buffer canaries) is a drop-in
+    checked = ctypes.CDLL(_build.build(checked=True))
+    missing = [n for n in _declared() if not hasattr(checked, n)]
+    assert not missing, missing
+    checked.sph_strerror.restype = ctypes.c_char_p
+    checked.sph_strerror.argtypes = [ctypes.c_int]
+    assert b"checked build" in checked.sph_strerror(-10)
