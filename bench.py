@@ -48,6 +48,9 @@ def make_workload(name):
                 "dam_break_16M: tank 1.6x0.67x0.6 m, column 0.4x0.67x0.3 m, dp 1.71 mm")
     if name == "box":
         return scenes.periodic_box(n_per_axis=16), "periodic_box_4096: 16^3 lattice, dp 0.02 m"
+    if name == "box2m":
+        return (scenes.periodic_box(n_per_axis=128, jitter=0.1),
+                "periodic_box_2M: 128^3 lattice (jitter 0.1 dp), dp 0.02 m, all fluid, 80 neighbours")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -569,7 +572,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box", "batch", "adjoint"])
+    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box", "box2m", "batch", "adjoint"])
     ap.add_argument("--max-neibs", type=int, default=128)
     ap.add_argument("--profile-steps", type=int, default=50)
     ap.add_argument("--e2e-steps", type=int, default=20)
