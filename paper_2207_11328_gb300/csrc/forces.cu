@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
     uint32_t* __restrict__ ncount_x) {
     constexpr bool FILTER = SKIN && MODE != kCorrect;
     constexpr bool COMPACT = SKIN && MODE == kPredict;
+    constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -106,19 +107,46 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
         const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
         Acc acc{0.f, 0.f, 0.f, 0.f};
         const size_t S = ph.stride;
-        uint32_t* xf = COMPACT ? nlist_x + i : nullptr;  // exact list: next fluid / boundary slot
-        uint32_t* xb = COMPACT ? nlist_x + (size_t)(ph.max_neibs - 1) * S + i : nullptr;
-        uint32_t nxf = 0, nxb = 0;
-        if (fluid_i) {
+        const uint32_t kxb = exact_bnd_chunk(ph.max_neibs);
+        ChunkWriter xf{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x), S, i};
+        ChunkWriter xb{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x) + (size_t)kxb * S, S, i};
+        if (fluid_i && CHUNKED) {
+            const float phat_i = phat[i];
+            const float pic = sc.pi_coef;
+            const Central ci = central_of(pi, cx, cy, cz);
+            const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;
+            uint32_t k = 0;
+            for (; k < nf; k += 4, cp += S) {
+                const uint4 q = __ldg(cp);
+                SPH_GUARD((q.x >> kCodeBits) < n, st, break)
+                fluid_pair<VISC, false, false>(q.x, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 1 < nf) fluid_pair<VISC, false, false>(q.y, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 2 < nf) fluid_pair<VISC, false, false>(q.z, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 3 < nf) fluid_pair<VISC, false, false>(q.w, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+            }
+            cp = reinterpret_cast<const uint4*>(nlist) + (size_t)kxb * S + i;
+            for (k = 0; k < nb; k += 4, cp += S) {
+                const uint4 q = __ldg(cp);
+                SPH_GUARD((q.x >> kCodeBits) < n, st, break)
+                fluid_pair<VISC, true, false>(q.x, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 1 < nb) fluid_pair<VISC, true, false>(q.y, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 2 < nb) fluid_pair<VISC, true, false>(q.z, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                if (k + 3 < nb) fluid_pair<VISC, true, false>(q.w, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+            }
+            acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
+            acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
+            acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
+            acc.drho *= ph.aF;
+        } else if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
             const Central ci = central_of(pi, cx, cy, cz);
             // list entries come from DRAM: load four slots ahead of their use
             const uint32_t* lp = nlist + i;
             uint32_t k = 0;
-// keep a pair of the exact list (COMPACT only; fluid slots upwards, boundary downwards)
-#define SPH_KEEP_F(e) if (COMPACT) { *xf = (e); xf += S; ++nxf; }
-#define SPH_KEEP_B(e) if (COMPACT) { *xb = (e); xb -= S; ++nxb; }
+// keep a pair of the exact list (COMPACT only)
+#define SPH_KEEP_F(e) if (COMPACT) xf.put(e);
+#define SPH_KEEP_B(e) if (COMPACT) xb.put(e);
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
                 SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
@@ -153,9 +181,20 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             // boundary particle: continuity over its fluid neighbours, u_i = 0
             const Central ci = central_of(pi, cx, cy, cz);
             const uint32_t* lp = nlist + i;
+            const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;  // chunked exact list
+            uint4 q = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll 2
             for (uint32_t k = 0; k < nf; ++k, lp += S) {
-                const uint32_t e = __ldg(lp);
+                uint32_t e;
+                if (CHUNKED) {
+                    if ((k & 3u) == 0u) {
+                        q = __ldg(cp);
+                        cp += S;
+                    }
+                    e = (k & 3u) == 0u ? q.x : ((k & 3u) == 1u ? q.y : ((k & 3u) == 2u ? q.z : q.w));
+                } else {
+                    e = __ldg(lp);
+                }
                 const uint32_t j = e >> kCodeBits;
                 SPH_GUARD(j < n, st, continue)
                 const float4 pj = pos[j];
@@ -180,11 +219,9 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
 #undef SPH_KEEP_F
 #undef SPH_KEEP_B
         if (COMPACT) {
-            if (nxf + nxb < ph.max_neibs) {
-                *xf = kMarker;
-                *xb = kMarker;
-            }
-            ncount_x[i] = nxf | (nxb << 16);
+            xf.flush();
+            xb.flush();
+            ncount_x[i] = xf.n | (xb.n << 16);
         }
 
         // epilogue written out here rather than through finish_particle() of

@@ -28,6 +28,40 @@ __device__ __forceinline__ float pick(uint32_t b, float m, float z, float p) {
     return (b & 1u) ? z : ((b & 2u) ? p : m);
 }
 
+// The exact list of a skin-list step (written by the predictor pass, read by the
+// corrector): entries in chunks of four, chunk g of particle i at uint4 index
+// g * stride + i, fluid entries from chunk 0 and boundary entries from chunk
+// exact_bnd_chunk(max_neibs).  A lane writes a chunk with one 16-byte store once
+// it holds four entries (the entries of a list are found at different times in
+// different lanes, so 4-byte stores would scatter); the corrector reads four
+// entries per coalesced 16-byte load.  Unused slots of the last chunk hold kMarker.
+
+struct ChunkWriter {
+    uint4 buf;      // the last entries, newest in .w
+    uint32_t n;     // entries written
+    uint4* base;    // chunk 0 of particle 0 of this part
+    size_t stride;
+    uint32_t i;
+    __device__ __forceinline__ void put(uint32_t e) {
+        buf.x = buf.y;
+        buf.y = buf.z;
+        buf.z = buf.w;
+        buf.w = e;
+        if ((++n & 3u) == 0u) base[(size_t)((n >> 2) - 1u) * stride + i] = buf;
+    }
+    __device__ __forceinline__ void flush() {
+        const uint32_t r = n & 3u;  // the last r entries sit in the top r slots
+        if (r) {
+            uint4 o;
+            o.x = r == 1u ? buf.w : (r == 2u ? buf.z : buf.y);
+            o.y = r == 1u ? kMarker : (r == 2u ? buf.w : buf.z);
+            o.z = r == 3u ? buf.w : kMarker;
+            o.w = kMarker;
+            base[(size_t)(n >> 2) * stride + i] = o;
+        }
+    }
+};
+
 // Epilogue of particle i with its summed rates acc (a and drho/dt).
 //   kForcesOnly: store (a, drho/dt);
 //   kPredict:    u* = u + dt/2 a, delta* = delta + dt/2 drho/rho0, x* = x + dt/2 u  -> io_*

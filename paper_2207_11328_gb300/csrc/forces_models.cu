@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
     // pairs within it (the step's exact list) for the corrector, which reads that list as is
     const bool filter = skin && MODE != kCorrect;
     const bool compact = skin && MODE == kPredict;
+    const bool chunked = skin && MODE == kCorrect;  // nlist/ncount: that exact list, in chunks of four
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -142,18 +143,34 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
         const float ri = 1.0f + vi.w;
         const size_t S = ph.stride;
         Acc acc{0.f, 0.f, 0.f, 0.f};
-        uint32_t* xf = compact ? nlist_x + i : nullptr;  // exact list: next fluid / boundary slot
-        uint32_t* xb = compact ? nlist_x + (size_t)(ph.max_neibs - 1) * S + i : nullptr;
-        uint32_t nxf = 0, nxb = 0;
+        const uint32_t kxb = exact_bnd_chunk(ph.max_neibs);
+        ChunkWriter xf{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x), S, i};
+        ChunkWriter xb{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x) + (size_t)kxb * S, S, i};
+        // entry k of a part of the chunked exact list (first chunk c0)
+        auto chunk_entry = [&](uint32_t c0, uint32_t k) -> uint32_t {
+            return __ldg(nlist + ((size_t)(c0 + (k >> 2)) * S + i) * 4 + (k & 3u));
+        };
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef, ddc = sc.dd_coef;
             const uint32_t* lp = nlist + i;
             uint32_t k = 0;
-#define SPH_KEEP_F(e) if (compact) { *xf = (e); xf += S; ++nxf; }
-#define SPH_KEEP_B(e) if (compact) { *xb = (e); xb -= S; ++nxb; }
+#define SPH_KEEP_F(e) if (compact) xf.put(e);
+#define SPH_KEEP_B(e) if (compact) xb.put(e);
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
-                const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
+                uint32_t e0, e1, e2, e3;
+                if (chunked) {
+                    const uint4 q = __ldg(reinterpret_cast<const uint4*>(nlist) + (size_t)(k >> 2) * S + i);
+                    e0 = q.x;
+                    e1 = q.y;
+                    e2 = q.z;
+                    e3 = q.w;
+                } else {
+                    e0 = __ldg(lp);
+                    e1 = __ldg(lp + S);
+                    e2 = __ldg(lp + 2 * S);
+                    e3 = __ldg(lp + 3 * S);
+                }
                 SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
                 if (model_pair<KT, VISC, false>(e0, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e0)
                 if (model_pair<KT, VISC, false>(e1, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e1)
@@ -161,13 +178,13 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
                 if (model_pair<KT, VISC, false>(e3, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e3)
             }
             for (; k < nf; ++k, lp += S) {
-                const uint32_t e = __ldg(lp);
+                const uint32_t e = chunked ? chunk_entry(0u, k) : __ldg(lp);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, false>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e)
             }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             for (k = 0; k < nb; ++k, lp -= S) {
-                const uint32_t e = __ldg(lp);
+                const uint32_t e = chunked ? chunk_entry(kxb, k) : __ldg(lp);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, true>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_B(e)
             }
@@ -181,7 +198,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             const bool form2 = ph.form == SPH_FORM_2;
 #pragma unroll 2
             for (uint32_t k = 0; k < nf; ++k, lp += S) {
-                const uint32_t e = __ldg(lp);
+                const uint32_t e = chunked ? chunk_entry(0u, k) : __ldg(lp);
                 const uint32_t j = e >> kCodeBits;
                 SPH_GUARD(j < n, st, continue)
                 const float4 pj = pos[j];
@@ -205,11 +222,9 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
 #undef SPH_KEEP_F
 #undef SPH_KEEP_B
         if (compact) {
-            if (nxf + nxb < ph.max_neibs) {
-                *xf = kMarker;
-                *xb = kMarker;
-            }
-            ncount_x[i] = nxf | (nxb << 16);
+            xf.flush();
+            xb.flush();
+            ncount_x[i] = xf.n | (xb.n << 16);
         }
         finish_particle<MODE>(i, s, sc, pi, vi, fluid_i, acc, io_pos, io_vel, io_phat, force_out, dyn, st, ph,
                               acc_dt, pos_ref);

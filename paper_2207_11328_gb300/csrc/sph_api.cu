@@ -583,7 +583,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     }
     if (p->rebuild_every > 1)
         ok = ok && alloc((void**)&b.pos_ref, sizeof(float4) * cap) &&
-             alloc((void**)&b.nlist_x, sizeof(uint32_t) * (size_t)ph.stride * p->max_neibs) &&
+             alloc((void**)&b.nlist_x, sizeof(uint4) * 2 * (size_t)exact_bnd_chunk(p->max_neibs) * ph.stride) &&
              alloc((void**)&b.ncount_x, sizeof(uint32_t) * cap);
     ok = ok && alloc((void**)&b.pos_s, sizeof(float4) * cap) && alloc((void**)&b.vel_s, sizeof(float4) * cap) &&
          alloc((void**)&b.phat_s, sizeof(float) * cap) &&

@@ -27,6 +27,8 @@
 namespace sphg {
 
 constexpr uint32_t kMarker = 0xFFFFFFFFu;
+// skin list: first chunk (of four entries) of the boundary part of the step's exact list
+__host__ __device__ constexpr uint32_t exact_bnd_chunk(uint32_t max_neibs) { return (max_neibs + 3u) / 4u; }
 constexpr int kCodeBits = 6;
 constexpr uint32_t kMaxParticles = 1u << (32 - kCodeBits);
 
