@@ -12,10 +12,10 @@
 // One thread per particle, sorted order.  The neighbour list is read
 // neighbour-major (a warp reads 128 contiguous bytes per slot), fluid slots
 // from the front and boundary slots from the back (split list, Section 4),
-// each with its own loop.  Per neighbour the kernel gathers pos4 + vel4 +
-// P/rho^2 (36 bytes, served by L1/L2: neighbours of consecutive particles
-// are the same cell-sorted particles).  P/rho^2 is computed once per
-// particle by whichever kernel writes delta, not once per pair.
+// each with its own loop.  Per neighbour the kernel gathers pos4 + vel4
+// (32 bytes, served by L1/L2: neighbours of consecutive particles are the
+// same cell-sorted particles) and P_j/rho_j^2, which the passes over a list
+// built at this step recompute from delta_j instead (see fluid_pair).
 // The predictor (dt/2) and corrector (dt) updates of reading C6 are fused
 // into the epilogues of the two force passes; the corrector pass reduces
 // max |a|^2 per scene (warp reduction + one atomic) for the CFL dt (C7).
@@ -28,15 +28,19 @@ namespace {
 // One neighbour of a fluid particle.  BND: the neighbour is a boundary
 // particle (mass stored negated, velocity zero).  The kernel constant aF is
 // factored out of every term (all terms are linear in F) and applied once.
-template <int VISC, bool BND, bool FILTER>
+// RECOMP: P_j/rho_j^2 from delta_j (the function that stores the per-particle
+// value, so bit-identical to it) in place of a third gather.  Faster in the
+// passes over a list built at this step (1.5 % on the dam break, 6 % on the
+// all-fluid box); slower in the skin-list passes, which keep the gather.
+template <int VISC, bool BND, bool FILTER, bool RECOMP>
 __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i,
                                            const float4* __restrict__ pos, const float4* __restrict__ vel,
-                                           const float* __restrict__ phat, float pi_coef, const Phys& ph, Acc& acc,
-                                           uint32_t& npairs) {
+                                           const float* __restrict__ phat, float phat_coef, float pi_coef,
+                                           const Phys& ph, Acc& acc, uint32_t& npairs) {
     const uint32_t j = e >> kCodeBits;
     const float4 pj = pos[j];
-    const float4 vj = vel[j];       // all gathers issued together
-    const float phat_j = phat[j];
+    const float4 vj = vel[j];  // all gathers issued together
+    const float phat_j = RECOMP ? eos_phat(vj.w, ph, phat_coef) : phat[j];
     const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;
     const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
     const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
     constexpr bool FILTER = SKIN && MODE != kCorrect;
     constexpr bool COMPACT = SKIN && MODE == kPredict;
     constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
+    constexpr bool RECOMP = !SKIN;
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -119,19 +124,19 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             for (; k < nf; k += 4, cp += S) {
                 const uint4 q = __ldg(cp);
                 SPH_GUARD((q.x >> kCodeBits) < n, st, break)
-                fluid_pair<VISC, false, false>(q.x, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 1 < nf) fluid_pair<VISC, false, false>(q.y, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 2 < nf) fluid_pair<VISC, false, false>(q.z, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 3 < nf) fluid_pair<VISC, false, false>(q.w, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, false, false, RECOMP>(q.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 1 < nf) fluid_pair<VISC, false, false, RECOMP>(q.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 2 < nf) fluid_pair<VISC, false, false, RECOMP>(q.z, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 3 < nf) fluid_pair<VISC, false, false, RECOMP>(q.w, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
             }
             cp = reinterpret_cast<const uint4*>(nlist) + (size_t)kxb * S + i;
             for (k = 0; k < nb; k += 4, cp += S) {
                 const uint4 q = __ldg(cp);
                 SPH_GUARD((q.x >> kCodeBits) < n, st, break)
-                fluid_pair<VISC, true, false>(q.x, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 1 < nb) fluid_pair<VISC, true, false>(q.y, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 2 < nb) fluid_pair<VISC, true, false>(q.z, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
-                if (k + 3 < nb) fluid_pair<VISC, true, false>(q.w, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs);
+                fluid_pair<VISC, true, false, RECOMP>(q.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 1 < nb) fluid_pair<VISC, true, false, RECOMP>(q.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 2 < nb) fluid_pair<VISC, true, false, RECOMP>(q.z, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                if (k + 3 < nb) fluid_pair<VISC, true, false, RECOMP>(q.w, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
             }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
@@ -150,28 +155,28 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             for (; k + 4 <= nf; k += 4, lp += 4 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
                 SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
-                if (fluid_pair<VISC, false, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e0)
-                if (fluid_pair<VISC, false, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e1)
-                if (fluid_pair<VISC, false, FILTER>(e2, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e2)
-                if (fluid_pair<VISC, false, FILTER>(e3, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e3)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(e0, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e0)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(e1, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e1)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(e2, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e2)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(e3, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e3)
             }
             for (; k < nf; ++k, lp += S) {
                 const uint32_t e = __ldg(lp);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
-                if (fluid_pair<VISC, false, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_F(e)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e)
             }
             lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
             k = 0;
             for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
                 const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
                 SPH_GUARD((max(e0, e1) >> kCodeBits) < n, st, break)
-                if (fluid_pair<VISC, true, FILTER>(e0, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e0)
-                if (fluid_pair<VISC, true, FILTER>(e1, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e1)
+                if (fluid_pair<VISC, true, FILTER, RECOMP>(e0, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e0)
+                if (fluid_pair<VISC, true, FILTER, RECOMP>(e1, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e1)
             }
             for (; k < nb; ++k, lp -= S) {
                 const uint32_t e = __ldg(lp);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
-                if (fluid_pair<VISC, true, FILTER>(e, ci, vi, phat_i, pos, vel, phat, pic, ph, acc, npairs)) SPH_KEEP_B(e)
+                if (fluid_pair<VISC, true, FILTER, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e)
             }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);

@@ -112,13 +112,16 @@ const char* forces_variant_name(int v);
 
 // P/rho^2 of Cole's EOS from delta = rho/rho0 - 1 (binomial form, no
 // cancellation near rest): phat_coef * delta * sum_k C(gamma,k) delta^(k-1) / (1+delta)^2.
-// Stored per particle by every kernel that writes delta.
+// Stored per particle by every kernel that writes delta, and recomputed from a
+// neighbour's delta by the tuned force kernels (one function, so both agree
+// bit for bit).  The quotient is __fdividef (reciprocal and product, within
+// 2 ulp for (1+delta)^2 in (2^-126, 2^126)): no slow-path call in the pair loop.
 __device__ __forceinline__ float eos_phat(float d, const Phys& ph, float phat_coef) {
     float poly = ph.coef[7];
 #pragma unroll
     for (int k = 6; k >= 0; --k) poly = fmaf(poly, d, ph.coef[k]);
     const float opd = 1.0f + d;
-    return phat_coef * d * poly / (opd * opd);
+    return __fdividef(phat_coef * d * poly, opd * opd);
 }
 
 // ---- checked build ----------------------------------------------------
