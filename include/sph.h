@@ -198,8 +198,9 @@ int sph_upload_device(sph_ctx* ctx, uint32_t n, const double* pos_dev, const flo
 
 /* Neighbour pipeline on the current state: cell hash, key sort by (cell,
  * type, id), reorder, cell start/end, split neighbour list (paper
- * Sections 2.3 and 4: fixed-size, neighbour-major, fluid neighbours from the
- * front and boundary neighbours from the back, end-of-list markers). */
+ * Sections 2.3 and 4: fixed-size, neighbour-major in chunks of two entries,
+ * fluid neighbours from the front and boundary neighbours from the back;
+ * sph_download_neighbors returns it by upload id). */
 int sph_build_neighbors(sph_ctx* ctx, void* stream);
 
 /* Particle interactions on the current state with the current neighbour

@@ -268,8 +268,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
         const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
         float gx = 0.f, gy = 0.f, gz = 0.f, gux = 0.f, guy = 0.f, guz = 0.f, gd = 0.f, ga = 0.f;
         for (uint32_t q = 0; q < nf + nb; ++q) {
-            const uint32_t slot = q < nf ? q : ph.max_neibs - 1 - (q - nf);
-            const uint32_t e = nlist[(size_t)slot * ph.stride + k];
+            const uint32_t e = nlist[q < nf ? list_fluid_word(q, k, ph.stride)
+                                            : list_bnd_word(q - nf, k, ph.stride, ph.max_neibs)];
             const uint32_t j = e >> kCodeBits;
             SPH_GUARD(j < st->n_active, st, continue)
             const float4 pj = pos[j];

@@ -10,9 +10,9 @@
 //   Dynamic boundary particles: zero velocity, continuity only      (C5)
 //
 // One thread per particle, sorted order.  The neighbour list is read
-// neighbour-major (a warp reads 128 contiguous bytes per slot), fluid slots
-// from the front and boundary slots from the back (split list, Section 4),
-// each with its own loop.  Per neighbour the kernel gathers pos4 + vel4
+// neighbour-major (a warp reads 256 contiguous bytes per two-entry chunk),
+// fluid chunks from the front and boundary chunks from the back (split list,
+// Section 4), each with its own loop.  Per neighbour the kernel gathers pos4 + vel4
 // (32 bytes, served by L1/L2: neighbours of consecutive particles are the
 // same cell-sorted particles) and P_j/rho_j^2, which the passes over a list
 // built at this step recompute from delta_j instead (see fluid_pair).
@@ -146,37 +146,34 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
             const Central ci = central_of(pi, cx, cy, cz);
-            // list entries come from DRAM: load four slots ahead of their use
-            const uint32_t* lp = nlist + i;
+            // list chunks come from DRAM: two chunks (four entries) in flight per iteration
+            const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;
             uint32_t k = 0;
 // keep a pair of the exact list (COMPACT only)
 #define SPH_KEEP_F(e) if (COMPACT) xf.put(e);
 #define SPH_KEEP_B(e) if (COMPACT) xb.put(e);
-            for (; k + 4 <= nf; k += 4, lp += 4 * S) {
-                const uint32_t e0 = __ldg(lp), e1 = __ldg(lp + S), e2 = __ldg(lp + 2 * S), e3 = __ldg(lp + 3 * S);
-                SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(e0, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e0)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(e1, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e1)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(e2, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e2)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(e3, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e3)
+            for (; k + 4 <= nf; k += 4, lp += 2 * S) {
+                const uint2 a = __ldg(lp), b = __ldg(lp + S);
+                SPH_GUARD((max(max(a.x, a.y), max(b.x, b.y)) >> kCodeBits) < n, st, break)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(b.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.x)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(b.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.y)
             }
-            for (; k < nf; ++k, lp += S) {
-                const uint32_t e = __ldg(lp);
-                SPH_GUARD((e >> kCodeBits) < n, st, continue)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(e)
+            for (; k < nf; k += 2, lp += S) {
+                const uint2 a = __ldg(lp);
+                const bool two = k + 1 < nf;
+                SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
+                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
+                if (two && fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
             }
-            lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
-            k = 0;
-            for (; k + 2 <= nb; k += 2, lp -= 2 * S) {
-                const uint32_t e0 = __ldg(lp), e1 = __ldg(lp - S);
-                SPH_GUARD((max(e0, e1) >> kCodeBits) < n, st, break)
-                if (fluid_pair<VISC, true, FILTER, RECOMP>(e0, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e0)
-                if (fluid_pair<VISC, true, FILTER, RECOMP>(e1, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e1)
-            }
-            for (; k < nb; ++k, lp -= S) {
-                const uint32_t e = __ldg(lp);
-                SPH_GUARD((e >> kCodeBits) < n, st, continue)
-                if (fluid_pair<VISC, true, FILTER, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(e)
+            lp = reinterpret_cast<const uint2*>(nlist) + (size_t)(list_chunks(ph.max_neibs) - 1u) * S + i;
+            for (k = 0; k < nb; k += 2, lp -= S) {
+                const uint2 a = __ldg(lp);
+                const bool two = k + 1 < nb;
+                SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
+                if (fluid_pair<VISC, true, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.x)
+                if (two && fluid_pair<VISC, true, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.y)
             }
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
@@ -185,11 +182,12 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
         } else {
             // boundary particle: continuity over its fluid neighbours, u_i = 0
             const Central ci = central_of(pi, cx, cy, cz);
-            const uint32_t* lp = nlist + i;
+            const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;  // list of the build
             const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;  // chunked exact list
             uint4 q = make_uint4(0u, 0u, 0u, 0u);
+            uint2 q2 = make_uint2(0u, 0u);
 #pragma unroll 2
-            for (uint32_t k = 0; k < nf; ++k, lp += S) {
+            for (uint32_t k = 0; k < nf; ++k) {
                 uint32_t e;
                 if (CHUNKED) {
                     if ((k & 3u) == 0u) {
@@ -198,7 +196,11 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
                     }
                     e = (k & 3u) == 0u ? q.x : ((k & 3u) == 1u ? q.y : ((k & 3u) == 2u ? q.z : q.w));
                 } else {
-                    e = __ldg(lp);
+                    if ((k & 1u) == 0u) {
+                        q2 = __ldg(lp);
+                        lp += S;
+                    }
+                    e = (k & 1u) ? q2.y : q2.x;
                 }
                 const uint32_t j = e >> kCodeBits;
                 SPH_GUARD(j < n, st, continue)

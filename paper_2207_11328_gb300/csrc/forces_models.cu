@@ -146,18 +146,24 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
         const uint32_t kxb = exact_bnd_chunk(ph.max_neibs);
         ChunkWriter xf{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x), S, i};
         ChunkWriter xb{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x) + (size_t)kxb * S, S, i};
-        // entry k of a part of the chunked exact list (first chunk c0)
-        auto chunk_entry = [&](uint32_t c0, uint32_t k) -> uint32_t {
-            return __ldg(nlist + ((size_t)(c0 + (k >> 2)) * S + i) * 4 + (k & 3u));
+        // entry k of the fluid / boundary part: the list of the build (two-entry
+        // chunks, boundary part from the back) or, in the skin-list corrector, the
+        // step's exact list (four-entry chunks, boundary part from chunk kxb)
+        auto fluid_entry = [&](uint32_t k) -> uint32_t {
+            return chunked ? __ldg(nlist + ((size_t)(k >> 2) * S + i) * 4 + (k & 3u))
+                           : __ldg(nlist + list_fluid_word(k, i, S));
+        };
+        auto bnd_entry = [&](uint32_t k) -> uint32_t {
+            return chunked ? __ldg(nlist + ((size_t)(kxb + (k >> 2)) * S + i) * 4 + (k & 3u))
+                           : __ldg(nlist + list_bnd_word(k, i, S, ph.max_neibs));
         };
         if (fluid_i) {
             const float phat_i = phat[i];
             const float pic = sc.pi_coef, ddc = sc.dd_coef;
-            const uint32_t* lp = nlist + i;
             uint32_t k = 0;
 #define SPH_KEEP_F(e) if (compact) xf.put(e);
 #define SPH_KEEP_B(e) if (compact) xb.put(e);
-            for (; k + 4 <= nf; k += 4, lp += 4 * S) {
+            for (; k + 4 <= nf; k += 4) {
                 uint32_t e0, e1, e2, e3;
                 if (chunked) {
                     const uint4 q = __ldg(reinterpret_cast<const uint4*>(nlist) + (size_t)(k >> 2) * S + i);
@@ -166,10 +172,12 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
                     e2 = q.z;
                     e3 = q.w;
                 } else {
-                    e0 = __ldg(lp);
-                    e1 = __ldg(lp + S);
-                    e2 = __ldg(lp + 2 * S);
-                    e3 = __ldg(lp + 3 * S);
+                    const uint2* lp = reinterpret_cast<const uint2*>(nlist) + (size_t)(k >> 1) * S + i;
+                    const uint2 a = __ldg(lp), b = __ldg(lp + S);
+                    e0 = a.x;
+                    e1 = a.y;
+                    e2 = b.x;
+                    e3 = b.y;
                 }
                 SPH_GUARD((max(max(e0, e1), max(e2, e3)) >> kCodeBits) < n, st, break)
                 if (model_pair<KT, VISC, false>(e0, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e0)
@@ -177,14 +185,13 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
                 if (model_pair<KT, VISC, false>(e2, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e2)
                 if (model_pair<KT, VISC, false>(e3, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e3)
             }
-            for (; k < nf; ++k, lp += S) {
-                const uint32_t e = chunked ? chunk_entry(0u, k) : __ldg(lp);
+            for (; k < nf; ++k) {
+                const uint32_t e = fluid_entry(k);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, false>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_F(e)
             }
-            lp = nlist + (size_t)(ph.max_neibs - 1) * S + i;
-            for (k = 0; k < nb; ++k, lp -= S) {
-                const uint32_t e = chunked ? chunk_entry(kxb, k) : __ldg(lp);
+            for (k = 0; k < nb; ++k) {
+                const uint32_t e = bnd_entry(k);
                 SPH_GUARD((e >> kCodeBits) < n, st, continue)
                 if (model_pair<KT, VISC, true>(e, ci, vi, phat_i, ri, pos, vel, phat, pic, ddc, ph, filter, acc, npairs)) SPH_KEEP_B(e)
             }
@@ -194,11 +201,10 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             acc.drho *= ph.aF;
         } else {
             // boundary particle: continuity over its fluid neighbours, u_i = 0
-            const uint32_t* lp = nlist + i;
             const bool form2 = ph.form == SPH_FORM_2;
 #pragma unroll 2
-            for (uint32_t k = 0; k < nf; ++k, lp += S) {
-                const uint32_t e = chunked ? chunk_entry(0u, k) : __ldg(lp);
+            for (uint32_t k = 0; k < nf; ++k) {
+                const uint32_t e = fluid_entry(k);
                 const uint32_t j = e >> kCodeBits;
                 SPH_GUARD(j < n, st, continue)
                 const float4 pj = pos[j];

@@ -323,11 +323,7 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
         if (total == 0) {
             for (uint32_t base = b0; base < e0; base += 32) {
                 const uint32_t i = base + lane;
-                if (i < e0) {
-                    nlist[i] = kMarker;
-                    nlist[(size_t)(max_neibs - 1) * stride + i] = kMarker;
-                    ncount[i] = 0u;
-                }
+                if (i < e0) ncount[i] = 0u;
             }
             continue;
         }
@@ -338,9 +334,9 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
             const bool fluid_i = active && pi.w > 0.f;
             // parked lanes sit far away on one side, padding candidates on the other
             const float px = active ? pi.x : 3.0e18f, py = pi.y, pz = pi.z;
-            uint32_t nfw = 0, nbw = 0, nfound = 0;
-            uint32_t* pf = nlist + i;                                     // next fluid slot
-            uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;  // next boundary slot
+            uint32_t nfound = 0;
+            ListWriter wf = list_fluid_writer(nlist, i, stride);
+            ListWriter wb = list_bnd_writer(nlist, i, stride, max_neibs);
             for (uint32_t w0 = 0; w0 < total; w0 += kStage) {
                 const uint32_t w1 = min(total, w0 + (uint32_t)kStage);
                 __syncwarp();
@@ -385,20 +381,16 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
                     uint32_t hb = fluid_i ? hits & ~fmask : 0u;
                     const uint32_t cf = __popc(hf), cb = __popc(hb);
                     nfound += cf + cb;
-                    if (nfw + nbw + cf + cb <= max_neibs) {
-                        nfw += cf;
-                        nbw += cb;
+                    if (wf.n + wb.n + cf + cb <= max_neibs) {
                         while (hf) {
                             const int u = __ffs(hf) - 1;
                             hf &= hf - 1u;
-                            *pf = e_s[kb32 + u];
-                            pf += stride;
+                            wf.put(e_s[kb32 + u]);
                         }
                         while (hb) {
                             const int u = __ffs(hb) - 1;
                             hb &= hb - 1u;
-                            *pb = e_s[kb32 + u];
-                            pb -= stride;
+                            wb.put(e_s[kb32 + u]);
                         }
                     } else {
                         // list full: keep the first hits in candidate order, count the rest
@@ -406,30 +398,23 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
                         while (h) {
                             const int u = __ffs(h) - 1;
                             h &= h - 1u;
-                            if (nfw + nbw >= max_neibs) break;
-                            if ((fmask >> u) & 1u) {
-                                *pf = e_s[kb32 + u];
-                                pf += stride;
-                                ++nfw;
-                            } else {
-                                *pb = e_s[kb32 + u];
-                                pb -= stride;
-                                ++nbw;
-                            }
+                            if (wf.n + wb.n >= max_neibs) break;
+                            if ((fmask >> u) & 1u)
+                                wf.put(e_s[kb32 + u]);
+                            else
+                                wb.put(e_s[kb32 + u]);
                         }
                     }
                 }
             }
             if (active) {
-                if (nfw + nbw < max_neibs) {
-                    *pf = kMarker;
-                    *pb = kMarker;
-                }
-                ncount[i] = nfw | (nbw << 16);
+                wf.flush();
+                wb.flush();
+                ncount[i] = wf.n | (wb.n << 16);
                 if (nfound > max_neibs) atomicOr(&st->error_bits, SPH_EBIT_NEIB_OVERFLOW);
             }
             const uint32_t m = __reduce_max_sync(0xffffffffu, active ? nfound : 0u);
-            const uint32_t wsum = __reduce_add_sync(0xffffffffu, active ? nfw + nbw : 0u);
+            const uint32_t wsum = __reduce_add_sync(0xffffffffu, active ? wf.n + wb.n : 0u);
             if (lane == 0) {
                 atomicMax(&st->max_neibs_seen, m);
                 atomicAdd(&st->list_entries, (unsigned long long)wsum);
@@ -462,9 +447,9 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
     const bool fluid_i = pi.w > 0.f;
     int cx, cy, cz;
     decode_local(cell[i] - sc.cell_offset, sc, cx, cy, cz);
-    uint32_t nfw = 0, nbw = 0, nfound = 0;
-    uint32_t* pf = nlist + i;
-    uint32_t* pb = nlist + (size_t)(max_neibs - 1) * stride + i;
+    uint32_t nfound = 0;
+    ListWriter wf = list_fluid_writer(nlist, i, stride);
+    ListWriter wb = list_bnd_writer(nlist, i, stride, max_neibs);
     for (int dz = -1; dz <= 1; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= sc.ncell[2]) {
@@ -531,32 +516,22 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                     while (hf) {
                         const int u = __ffs(hf) - 1;
                         hf &= hf - 1u;
-                        if (nfw + nbw < max_neibs) {
-                            *pf = ((j + u) << kCodeBits) | code;
-                            pf += stride;
-                            ++nfw;
-                        }
+                        if (wf.n + wb.n < max_neibs) wf.put(((j + u) << kCodeBits) | code);
                     }
                     while (hb) {
                         const int u = __ffs(hb) - 1;
                         hb &= hb - 1u;
-                        if (nfw + nbw < max_neibs) {
-                            *pb = ((j + u) << kCodeBits) | code;
-                            pb -= stride;
-                            ++nbw;
-                        }
+                        if (wf.n + wb.n < max_neibs) wb.put(((j + u) << kCodeBits) | code);
                     }
                 }
             }
         }
     }
-    if (nfw + nbw < max_neibs) {
-        *pf = kMarker;
-        *pb = kMarker;
-    }
-    ncount[i] = nfw | (nbw << 16);
+    wf.flush();
+    wb.flush();
+    ncount[i] = wf.n | (wb.n << 16);
     *nfound_out = nfound;
-    return nfw + nbw;
+    return wf.n + wb.n;
 }
 
 // warp-level list statistics: overflow flag, largest count, entries written

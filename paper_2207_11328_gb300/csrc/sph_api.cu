@@ -251,9 +251,8 @@ __global__ void k_download_neighbors(const uint32_t* __restrict__ nlist, const u
         counts[2 * (size_t)id] = nf;
         counts[2 * (size_t)id + 1] = nb;
         uint32_t* out = ids + (size_t)id * max_neibs;
-        for (uint32_t k = 0; k < nf; ++k) out[k] = pid[nlist[(size_t)k * stride + i] >> kCodeBits];
-        for (uint32_t k = 0; k < nb; ++k)
-            out[nf + k] = pid[nlist[(size_t)(max_neibs - 1 - k) * stride + i] >> kCodeBits];
+        for (uint32_t k = 0; k < nf; ++k) out[k] = pid[nlist[list_fluid_word(k, i, stride)] >> kCodeBits];
+        for (uint32_t k = 0; k < nb; ++k) out[nf + k] = pid[nlist[list_bnd_word(k, i, stride, max_neibs)] >> kCodeBits];
     }
 }
 
@@ -589,7 +588,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
          alloc((void**)&b.phat_s, sizeof(float) * cap) &&
          alloc((void**)&b.force, sizeof(float4) * cap) && alloc((void**)&b.key, sizeof(uint32_t) * cap) &&
          alloc((void**)&b.slot, sizeof(uint32_t) * cap) && alloc((void**)&b.unsorted, sizeof(uint32_t) * cap) &&
-         alloc((void**)&b.nlist, sizeof(uint32_t) * (size_t)ph.stride * p->max_neibs) &&
+         alloc((void**)&b.nlist, sizeof(uint2) * (size_t)ph.stride * list_chunks(p->max_neibs)) &&
          alloc((void**)&b.ncount, sizeof(uint32_t) * cap) && alloc((void**)&b.status, sizeof(DevStatus));
     c->staging_bytes = 64 * (size_t)cap + 32768;  // >= the conservation sums' scratch
     ok = ok && alloc(&b.staging, c->staging_bytes);

@@ -11,15 +11,17 @@
 //            accuracy in P, which absolute rho ~ 1000 would not).
 //   cell[i]  u32 global cell key (scene cell offset + linear cell index).
 //   pinfo[i] u32 scene index.   pid[i] u32 upload id.
-//   nlist    u32[max_neibs * stride], neighbour-major (entry k of particle i
-//            at k*stride + i, paper Section 4 "interleaved" layout); fluid
-//            neighbours from slot 0 up, boundary neighbours from slot
-//            max_neibs-1 down, 0xFFFFFFFF end markers.  Entry = j << 6 | code,
+//   nlist    uint2[list_chunks(max_neibs) * stride], neighbour-major in
+//            chunks of two entries (chunk c of particle i at c*stride + i:
+//            the paper's Section 4 "interleaved" layout, two slots wide);
+//            fluid neighbours from chunk 0 up, boundary neighbours from the
+//            last chunk down (see list_chunks).  Entry = j << 6 | code,
 //            code = 2 bits per axis of the cell delta (d+1), so the
 //            separation is x_ij = o_i - o_j - d * cell (periodic images too).
 //   ncount[i] u32 nf | nb << 16.
 #pragma once
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "sph.h"
@@ -31,6 +33,52 @@ constexpr uint32_t kMarker = 0xFFFFFFFFu;
 __host__ __device__ constexpr uint32_t exact_bnd_chunk(uint32_t max_neibs) { return (max_neibs + 3u) / 4u; }
 constexpr int kCodeBits = 6;
 constexpr uint32_t kMaxParticles = 1u << (32 - kCodeBits);
+
+// ---- neighbour list layout ------------------------------------------------
+// Two entries per chunk (uint2): a particle's entries leave the build in
+// 8-byte stores and a warp of consecutive particles reads 256 contiguous
+// bytes per chunk.  Fluid entries fill chunks 0, 1, 2, ..., boundary entries
+// chunks C-1, C-2, ... with C = list_chunks(max_neibs) chunks per particle:
+// every split nf + nb <= max_neibs fits, as ceil(nf/2) + ceil(nb/2) <=
+// (nf + nb)/2 + 1.  The unused half of an odd last chunk holds kMarker.
+__host__ __device__ constexpr uint32_t list_chunks(uint32_t max_neibs) { return (max_neibs + 1u) / 2u + 1u; }
+
+// u32 index of entry k of the fluid / boundary part of particle i's list
+__host__ __device__ inline size_t list_fluid_word(uint32_t k, uint32_t i, size_t stride) {
+    return 2 * ((size_t)(k >> 1) * stride + i) + (k & 1u);
+}
+__host__ __device__ inline size_t list_bnd_word(uint32_t k, uint32_t i, size_t stride, uint32_t max_neibs) {
+    return 2 * ((size_t)(list_chunks(max_neibs) - 1u - (k >> 1)) * stride + i) + (k & 1u);
+}
+
+// One part (fluid or boundary) of one particle's list, written entry by entry
+// by the thread that owns the particle: a chunk is stored once it is full.
+struct ListWriter {
+    uint2 buf;       // .y the newest entry
+    uint32_t n;      // entries written
+    uint2* p;        // the chunk being filled
+    ptrdiff_t step;  // +stride (fluid part) or -stride (boundary part), in chunks
+    __device__ __forceinline__ void put(uint32_t e) {
+        buf.x = buf.y;
+        buf.y = e;
+        if ((++n & 1u) == 0u) {
+            *p = buf;
+            p += step;
+        }
+    }
+    __device__ __forceinline__ void flush() {
+        if (n & 1u) *p = make_uint2(buf.y, kMarker);
+    }
+};
+__device__ __forceinline__ ListWriter list_fluid_writer(uint32_t* nlist, uint32_t i, size_t stride) {
+    return ListWriter{make_uint2(0u, 0u), 0u, reinterpret_cast<uint2*>(nlist) + i, (ptrdiff_t)stride};
+}
+__device__ __forceinline__ ListWriter list_bnd_writer(uint32_t* nlist, uint32_t i, size_t stride,
+                                                      uint32_t max_neibs) {
+    return ListWriter{make_uint2(0u, 0u), 0u,
+                      reinterpret_cast<uint2*>(nlist) + (size_t)(list_chunks(max_neibs) - 1u) * stride + i,
+                      -(ptrdiff_t)stride};
+}
 
 struct SceneDev {
     double origin[3];
