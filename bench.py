@@ -354,7 +354,14 @@ def run_ours(args, world, rank, local):
         args.max_neibs = max(args.max_neibs, int(128 * (1 + args.skin / 2) ** 3) // 32 * 32 + 32)
     sim = Simulation.from_scene(scene, max_neibs=args.max_neibs, stream=stream, rebuild_every=args.rebuild_every,
                                 skin=args.skin * scene.h)
-    tuned = sim.autotune(stream=stream)
+    if args.variants:
+        # shapes given (profiling under ncu, whose launch interception skews the tuner's timings)
+        vb, vp, vc = (int(x) for x in args.variants.split(","))
+        sim.set_variants(build=vb)
+        sim.set_forces_variants(vp, vc)
+    else:
+        sim.autotune(stream=stream)
+    tuned = sim.variants()
     sim.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     st0 = sim.stats(stream=stream)
@@ -431,7 +438,7 @@ def run_ours(args, world, rank, local):
                        "rebuild": "every step" if not skin_mode else
                                   f"every {args.rebuild_every} steps, list radius 2h + {args.skin}h",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
-                       "autotuned": {"build": tuned[0], "forces": tuned[1]}},
+                       "variants": dict(tuned, autotuned=not args.variants)},
             "particle_steps_per_s": psteps, "mean_neighbours": entries / max(1.0, psteps_local),
             "list_builds": st1["builds"] - st0["builds"],
             "roofline": roofline, "gpu_launches": int(kernels * args.steps),
@@ -481,7 +488,8 @@ def run_batch(args):
     b = scenes.sloshing_batch()
     stream = torch.cuda.current_stream()
     sim = Simulation.from_scene(b, stream=stream)
-    tuned = sim.autotune(stream=stream)
+    sim.autotune(stream=stream)
+    tuned = sim.variants()
     sim.step(args.warmup, stream=stream)
     torch.cuda.synchronize()
     st0 = sim.stats(stream=stream)
@@ -520,8 +528,8 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": 1e3 * t_b / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"sloshing_batch: {len(b.scenes)} tanks, {b.n} particles "
-                                   f"({b.n_fluid} fluid), dp 0.01 m", "autotuned": {"build": tuned[0],
-                                                                                  "forces": tuned[1]}},
+                                   f"({b.n_fluid} fluid), dp 0.01 m",
+                                   "variants": dict(tuned, autotuned=True)},
             "particle_steps_per_s": b.n * args.steps / t_b,
             "per_scene_launches": {"value": inter_p / t_p, "ms_per_step": 1e3 * t_p / ps_steps,
                                    "particle_steps_per_s": b.n * ps_steps / t_p, "steps": ps_steps},
@@ -575,6 +583,8 @@ def main():
     ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box", "box2m", "batch", "adjoint"])
     ap.add_argument("--max-neibs", type=int, default=128)
     ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--variants", default="",
+                    help="build,predictor,corrector variant indices (0..4) instead of autotuning")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rebuild-every", type=int, default=1,

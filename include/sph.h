@@ -249,19 +249,33 @@ int sph_backward(sph_ctx* ctx, const float* xbar_T, const float* ubar_T, const f
 /* Autotuner (launch shapes only; results are unchanged): times each
  * neighbour-build variant (one thread per particle with 128 or 256 threads
  * per block, or one warp per cell with 2, 4 or 8 cells per block) and each
- * force-kernel shape (64, 128 or 256 threads per block; 128 threads with a
- * register cap for 10 or 12 resident blocks per SM) on the uploaded state
- * (3 timed launches each, CUDA events on `stream`), keeps the fastest and
- * re-captures the step graph on the next sph_step.  Outputs (nullable): the
- * chosen variants (names: sph_build_variant_name, sph_forces_variant_name).
+ * force-kernel shape (64, 128 or 256 threads per block with at most 64
+ * registers; 128 threads with at most 85 or 128) on the uploaded state, the
+ * predictor and the corrector pass apart (3 timed launches each, CUDA events
+ * on `stream`; the corrector runs on a scratch copy of the state), keeps the
+ * fastest and re-captures the step graph on the next sph_step.  The
+ * particle state and the next time step are as before the call (the list
+ * counters include the timed builds).  Outputs (nullable): the build
+ * variant and the predictor pass's shape (names: sph_build_variant_name,
+ * sph_forces_variant_name; sph_get_variants gives the corrector's too).
  * Synchronises `stream`; SPH_ERR_STATE before an upload. */
 int sph_autotune(sph_ctx* ctx, void* stream, int* build_variant, int* forces_variant);
 
 /* Select the neighbour-build variant (0..4) and the force-kernel launch shape
- * (0..4) directly, as sph_autotune would (-1 keeps the current one).  Every
- * variant computes the same bits.  Synchronises the device; SPH_ERR_ARG for
- * an index out of range. */
+ * (0..4, for every pass) directly, as sph_autotune would (-1 keeps the
+ * current one).  Every variant computes the same bits.  Synchronises the
+ * device; SPH_ERR_ARG for an index out of range. */
 int sph_set_variants(sph_ctx* ctx, int build_variant, int forces_variant);
+
+/* The force-kernel launch shapes (0..4) of the forces-only and predictor
+ * passes and of the corrector pass, set apart (-1 keeps one).  sph_autotune
+ * picks them apart too: the fastest shape of the two passes can differ.
+ * Synchronises the device; SPH_ERR_ARG for an index out of range. */
+int sph_set_forces_variants(sph_ctx* ctx, int forces_predict, int forces_correct);
+
+/* The variants in use: build, predictor-pass shape, corrector-pass shape
+ * (outputs nullable). */
+int sph_get_variants(sph_ctx* ctx, int* build_variant, int* forces_predict, int* forces_correct);
 
 /* Names of the variants of sph_autotune (static storage). */
 const char* sph_build_variant_name(int variant);

@@ -98,6 +98,8 @@ _SIGS = {
     "sph_set_variants": [_vp, ctypes.c_int, ctypes.c_int],
     "sph_build_variant_name": [ctypes.c_int],
     "sph_forces_variant_name": [ctypes.c_int],
+    "sph_set_forces_variants": [_vp, ctypes.c_int, ctypes.c_int],
+    "sph_get_variants": [_vp, _vp, _vp, _vp],
     "sph_fp32_peak": [_vp, _vp],
     "sph_conservation": [_vp, _vp, _vp],
     "sph_strerror": [ctypes.c_int],
@@ -133,6 +135,20 @@ def fp32_peak(stream=None):
     t = ctypes.c_double()
     _check(_lib().sph_fp32_peak(_stream_handle(stream), ctypes.byref(t)), "sph_fp32_peak")
     return t.value
+
+
+N_BUILD_VARIANTS = 5   # sph_set_variants / sph_autotune indices 0..4
+N_FORCES_VARIANTS = 5
+
+
+def build_variant_names():
+    """Names of the neighbour-build variants, by index."""
+    return [_lib().sph_build_variant_name(v).decode() for v in range(N_BUILD_VARIANTS)]
+
+
+def forces_variant_names():
+    """Names of the force-kernel launch shapes, by index."""
+    return [_lib().sph_forces_variant_name(v).decode() for v in range(N_FORCES_VARIANTS)]
 
 
 def _check(rc, where):
@@ -315,8 +331,20 @@ class Simulation:
         return {"momentum": out[0:3], "force": out[3:6], "mass_rate": out[6], "kinetic": out[7]}
 
     def set_variants(self, build=-1, forces=-1):
-        """Select the build variant and force launch shape (0..4, -1 keeps)."""
+        """Select the build variant and force launch shape of every pass (0..4, -1 keeps)."""
         _check(_lib().sph_set_variants(self._h, int(build), int(forces)), "sph_set_variants")
+
+    def set_forces_variants(self, predict=-1, correct=-1):
+        """Select the force launch shapes of the predictor and corrector passes apart."""
+        _check(_lib().sph_set_forces_variants(self._h, int(predict), int(correct)), "sph_set_forces_variants")
+
+    def variants(self):
+        """Names of the variants in use: {"build", "forces_predict", "forces_correct"}."""
+        v = [ctypes.c_int() for _ in range(3)]
+        _check(_lib().sph_get_variants(self._h, *(ctypes.byref(x) for x in v)), "sph_get_variants")
+        return {"build": _lib().sph_build_variant_name(v[0].value).decode(),
+                "forces_predict": _lib().sph_forces_variant_name(v[1].value).decode(),
+                "forces_correct": _lib().sph_forces_variant_name(v[2].value).decode()}
 
     # ---- differentiable run ---------------------------------------------------
     def set_alpha(self, alpha):

@@ -29,9 +29,10 @@ namespace {
 // particle (mass stored negated, velocity zero).  The kernel constant aF is
 // factored out of every term (all terms are linear in F) and applied once.
 // RECOMP: P_j/rho_j^2 from delta_j (the function that stores the per-particle
-// value, so bit-identical to it) in place of a third gather.  Faster in the
-// passes over a list built at this step (1.5 % on the dam break, 6 % on the
-// all-fluid box); slower in the skin-list passes, which keep the gather.
+// value, so bit-identical to it) in place of a third gather.  Faster in every
+// pass over the pairs within the cutoff; slower in the passes that filter a
+// skin list (more registers live beside the exact-list writers), which keep
+// the gather.
 template <int VISC, bool BND, bool FILTER, bool RECOMP>
 __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const float4& vi, float phat_i,
                                            const float4* __restrict__ pos, const float4* __restrict__ vel,
@@ -97,7 +98,7 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
     constexpr bool FILTER = SKIN && MODE != kCorrect;
     constexpr bool COMPACT = SKIN && MODE == kPredict;
     constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
-    constexpr bool RECOMP = !SKIN;
+    constexpr bool RECOMP = !FILTER;  // P_j/rho_j^2 recomputed (see fluid_pair)
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -119,25 +120,47 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
             const Central ci = central_of(pi, cx, cy, cz);
+            // full chunks: four pairs with no test between them (their gathers issue together);
+            // then the last chunk of each part (1 to 3 entries, the rest kMarker)
+#define SPH_PAIR(BND, e) fluid_pair<VISC, BND, false, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)
+#define SPH_OK_E(e) (((e) >> kCodeBits) < n)
             const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;
             uint32_t k = 0;
-            for (; k < nf; k += 4, cp += S) {
+            for (; k + 4 <= nf; k += 4, cp += S) {
                 const uint4 q = __ldg(cp);
-                SPH_GUARD((q.x >> kCodeBits) < n, st, break)
-                fluid_pair<VISC, false, false, RECOMP>(q.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 1 < nf) fluid_pair<VISC, false, false, RECOMP>(q.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 2 < nf) fluid_pair<VISC, false, false, RECOMP>(q.z, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 3 < nf) fluid_pair<VISC, false, false, RECOMP>(q.w, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
+                SPH_PAIR(false, q.x);
+                SPH_PAIR(false, q.y);
+                SPH_PAIR(false, q.z);
+                SPH_PAIR(false, q.w);
             }
+            do {
+                if (k >= nf) break;
+                const uint4 q = __ldg(cp);
+                SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nf || SPH_OK_E(q.y)) && (k + 2 >= nf || SPH_OK_E(q.z)), st, break)
+                SPH_PAIR(false, q.x);
+                if (k + 1 < nf) SPH_PAIR(false, q.y);
+                if (k + 2 < nf) SPH_PAIR(false, q.z);
+            } while (0);
             cp = reinterpret_cast<const uint4*>(nlist) + (size_t)kxb * S + i;
-            for (k = 0; k < nb; k += 4, cp += S) {
+            for (k = 0; k + 4 <= nb; k += 4, cp += S) {
                 const uint4 q = __ldg(cp);
-                SPH_GUARD((q.x >> kCodeBits) < n, st, break)
-                fluid_pair<VISC, true, false, RECOMP>(q.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 1 < nb) fluid_pair<VISC, true, false, RECOMP>(q.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 2 < nb) fluid_pair<VISC, true, false, RECOMP>(q.z, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
-                if (k + 3 < nb) fluid_pair<VISC, true, false, RECOMP>(q.w, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs);
+                SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
+                SPH_PAIR(true, q.x);
+                SPH_PAIR(true, q.y);
+                SPH_PAIR(true, q.z);
+                SPH_PAIR(true, q.w);
             }
+            do {
+                if (k >= nb) break;
+                const uint4 q = __ldg(cp);
+                SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nb || SPH_OK_E(q.y)) && (k + 2 >= nb || SPH_OK_E(q.z)), st, break)
+                SPH_PAIR(true, q.x);
+                if (k + 1 < nb) SPH_PAIR(true, q.y);
+                if (k + 2 < nb) SPH_PAIR(true, q.z);
+            } while (0);
+#undef SPH_PAIR
+#undef SPH_OK_E
             acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
             acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
             acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
@@ -402,12 +425,12 @@ void launch_forces_b(const Buffers& b, int cur, const Geometry& g, const Phys& p
         launch_forces_s<VISC, B, MB, false>(b, cur, g, ph, mode, acc_dt, st);
 }
 
-// launch shapes of the force kernels (autotuned): threads per block and the
-// register cap implied by a minimum of resident blocks per SM
+// launch shapes of the force kernels (autotuned, the corrector pass on its own):
+// threads per block and the register cap implied by a minimum of resident blocks per SM
 template <int VISC>
 void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode, int acc_dt,
                      cudaStream_t st, bool skin) {
-    switch (ph.forces_variant) {
+    switch (mode == kCorrect ? ph.forces_variant_c : ph.forces_variant) {
         case 0: launch_forces_b<VISC, 64, 16>(b, cur, g, ph, mode, acc_dt, st, skin); break;
         case 2: launch_forces_b<VISC, 256, 4>(b, cur, g, ph, mode, acc_dt, st, skin); break;
         case 3: launch_forces_b<VISC, 128, 6>(b, cur, g, ph, mode, acc_dt, st, skin); break;

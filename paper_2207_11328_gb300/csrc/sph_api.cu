@@ -554,6 +554,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
     ph.gamma_i = (int)gm;
     ph.build_variant = 0;
     ph.forces_variant = 1;
+    ph.forces_variant_c = 1;
     const uint32_t cap = p->max_particles;
     ph.stride = (uint32_t)align_up(cap, 32);
     c->g.cap = cap;
@@ -786,6 +787,40 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
         }
     }
     c->ph.forces_variant = best_f;
+    // the corrector pass, on its own (its best shape differs from the predictor's): it runs
+    // on the predicted state the tuned predictor leaves, and reads state n from and writes
+    // n+1 to a copy in the sort's second buffer (free between builds); the per-scene |a|^2
+    // reduction and the status it updates are put back afterwards
+    int best_c = c->ph.forces_variant_c;
+    if (!c->ph.general) {
+        launch_forces(c->b, c->cur, c->g, c->ph, kPredict, 0, st);
+        const int alt = c->cur ^ 1;
+        const size_t cap = c->g.cap;
+        CK(cudaMemcpyAsync(c->b.pos[alt], c->b.pos[c->cur], sizeof(float4) * cap, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c->b.vel[alt], c->b.vel[c->cur], sizeof(float4) * cap, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c->b.phat[alt], c->b.phat[c->cur], sizeof(float) * cap, cudaMemcpyDeviceToDevice, st));
+        std::vector<SceneDyn> dyn_h(c->g.n_scenes);
+        DevStatus st_h;
+        CK(cudaMemcpyAsync(dyn_h.data(), c->b.dyn, sizeof(SceneDyn) * dyn_h.size(), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&st_h, c->b.status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        Buffers tb = c->b;
+        tb.pos[c->cur] = c->b.pos[alt];
+        tb.vel[c->cur] = c->b.vel[alt];
+        tb.phat[c->cur] = c->b.phat[alt];
+        best = 3.4e38f;
+        for (int v = 0; v < kForcesVariants; ++v) {
+            c->ph.forces_variant_c = v;
+            const float ms = time_ms([&] { launch_forces(tb, c->cur, c->g, c->ph, kCorrect, 0, st); });
+            if (ms < best) {
+                best = ms;
+                best_c = v;
+            }
+        }
+        CK(cudaMemcpyAsync(c->b.dyn, dyn_h.data(), sizeof(SceneDyn) * dyn_h.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(c->b.status, &st_h, sizeof(DevStatus), cudaMemcpyHostToDevice, st));
+    }
+    c->ph.forces_variant_c = best_c;
     c->fresh = true;  // the last build is of the current positions
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
@@ -797,12 +832,31 @@ int sph_autotune(sph_ctx* c, void* stream, int* build_variant, int* forces_varia
     return SPH_OK;
 }
 
+int sph_get_variants(sph_ctx* c, int* build_variant, int* forces_predict, int* forces_correct) {
+    if (!c) return SPH_ERR_ARG;
+    if (build_variant) *build_variant = c->ph.build_variant;
+    if (forces_predict) *forces_predict = c->ph.forces_variant;
+    if (forces_correct) *forces_correct = c->ph.forces_variant_c;
+    return SPH_OK;
+}
+
+int sph_set_forces_variants(sph_ctx* c, int forces_predict, int forces_correct) {
+    if (!c || forces_predict < -1 || forces_predict >= kForcesVariants || forces_correct < -1 ||
+        forces_correct >= kForcesVariants)
+        return SPH_ERR_ARG;
+    if (forces_predict >= 0) c->ph.forces_variant = forces_predict;
+    if (forces_correct >= 0) c->ph.forces_variant_c = forces_correct;
+    CK(cudaDeviceSynchronize());
+    drop_graphs(c);  // captured launches carry the old shapes
+    return SPH_OK;
+}
+
 int sph_set_variants(sph_ctx* c, int build_variant, int forces_variant) {
     if (!c || build_variant < -1 || build_variant >= kBuildVariants || forces_variant < -1 ||
         forces_variant >= kForcesVariants)
         return SPH_ERR_ARG;
     if (build_variant >= 0) c->ph.build_variant = build_variant;
-    if (forces_variant >= 0) c->ph.forces_variant = forces_variant;
+    if (forces_variant >= 0) c->ph.forces_variant = c->ph.forces_variant_c = forces_variant;
     CK(cudaDeviceSynchronize());
     drop_graphs(c);  // captured launches carry the old shapes
     return SPH_OK;
@@ -985,7 +1039,8 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     // (a training loop records and reverses the same configuration again and again)
     const bool reuse = t.steps && t.T == T && t.K == K && t.n == n && t.dt == dt &&
                        t.ph_rec.build_variant == c->ph.build_variant &&
-                       t.ph_rec.forces_variant == c->ph.forces_variant;
+                       t.ph_rec.forces_variant == c->ph.forces_variant &&
+                       t.ph_rec.forces_variant_c == c->ph.forces_variant_c;
     if (!reuse) free_tape(c);
     t.T = T;
     t.K = K;

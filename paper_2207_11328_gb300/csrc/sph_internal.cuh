@@ -142,7 +142,9 @@ struct Phys {
     uint32_t n_scenes;
     int gamma_i;             // EOS exponent (integer)
     int build_variant;       // neighbour-build kernel variant (autotuned), see build_variant_name
-    int forces_variant;      // launch shape of the force kernels (autotuned), see forces_variant_name
+    int forces_variant;      // launch shape of the forces-only and predictor passes (autotuned), see
+                             //   forces_variant_name
+    int forces_variant_c;    // launch shape of the corrector pass (autotuned on its own)
     // model options (Table 1); general != 0 selects the kernels of forces_models.cu
     int general;
     int kernel_type;         // SPH_KERNEL_*: F = aF f(q)

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
-from paper_2207_11328_gb300 import scenes
+from paper_2207_11328_gb300 import build_variant_names, forces_variant_names, scenes
 from tests.gpu_common import compare_neighbor_sets, rel_check, require_gpu, sim_for
 
 pytestmark = pytest.mark.gpu
@@ -197,3 +197,25 @@ def test_autotune_keeps_results_bitwise():
     assert np.array_equal(c0[0], c1[0]) and np.array_equal(c0[1], c1[1])
     sim.step(3)
     assert sim.stats()["steps"] == 3
+
+
+@pytest.mark.parametrize("skin", [0.0, 0.3])
+def test_autotune_leaves_the_run_unchanged(skin):
+    # the corrector shapes are timed on a scratch copy of the state: a run after the
+    # autotuner steps bit for bit like a run with the same shapes set by hand
+    s = _small_dam(dp=0.03)
+    kw = dict(rebuild_every=10, skin=skin * s.h, max_neibs=224) if skin else {}
+    a = sim_for(s, **kw)
+    a.autotune()
+    v = a.variants()
+    names = forces_variant_names()
+    b = sim_for(s, **kw)
+    b.set_variants(build=build_variant_names().index(v["build"]))
+    b.set_forces_variants(names.index(v["forces_predict"]), names.index(v["forces_correct"]))
+    assert b.variants() == v
+    a.step(6)
+    b.step(6)
+    for x, y in zip(a.download(), b.download()):
+        assert np.array_equal(x, y)
+    assert a.stats()["dt"] == b.stats()["dt"]
+    assert a.stats()["error_bits"] == 0
