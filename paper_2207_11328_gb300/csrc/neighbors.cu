@@ -467,6 +467,41 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
     uint32_t nfound = 0;
     ListWriter wf = list_fluid_writer(nlist, i, stride);
     ListWriter wb = list_bnd_writer(nlist, i, stride, max_neibs);
+    // candidates [b, e) of one neighbour cell and one type, appended to w in candidate order:
+    // groups of kGroup candidates (independent loads in flight), hits gathered in a bit mask.
+    // A group may read up to kGroup - 1 entries past the range (the next cell's, or the
+    // kPosPad spare entries at the end): masked off.  With room for the whole group the hits
+    // are appended by predicated puts (no loop whose trip count differs between lanes).
+    auto scan_part = [&](uint32_t b, uint32_t e, ListWriter& w, float bx, float by, float bz, uint32_t code) {
+        for (uint32_t j = b; j < e; j += kGroup) {
+            uint32_t hits = 0;
+            const float4* pg = pos + j;
+#pragma unroll
+            for (int u = 0; u < kGroup; ++u) {
+                const float4 pj = pg[u];
+                const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
+                hits |= (uint32_t)(__float_as_uint(r2) - 1u < r2lim) << u;
+            }
+            const uint32_t rem = e - j;
+            if (rem < (uint32_t)kGroup) hits &= (1u << rem) - 1u;
+            if (!hits) continue;
+            nfound += __popc(hits);
+            const uint32_t e0 = (j << kCodeBits) | code;
+            if (wf.n + wb.n + kGroup <= max_neibs) {
+#pragma unroll
+                for (int u = 0; u < kGroup; ++u)
+                    if ((hits >> u) & 1u) w.put(e0 + ((uint32_t)u << kCodeBits));
+            } else {
+                while (hits) {
+                    const int u = __ffs(hits) - 1;
+                    hits &= hits - 1u;
+                    if (wf.n + wb.n < max_neibs) w.put(e0 + ((uint32_t)u << kCodeBits));
+                }
+            }
+        }
+    };
     for (int dz = -1; dz <= 1; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= sc.ncell[2]) {
@@ -505,42 +540,12 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
                 const int dx = k - 1;
-                const uint32_t b = rb[k], ef = ref[k], e = re[k];
                 const float bx = pi.x - (float)dx * sc.cell_f[0];
                 const uint32_t code = (uint32_t)(dx + 1) | ((uint32_t)(dy + 1) << 2) | ((uint32_t)(dz + 1) << 4);
-                // groups of kGroup candidates: independent loads in flight, the hits
-                // gathered in a bit mask, then appended fluid-first in candidate order.
-                // A group may read up to kGroup - 1 entries past the cell (the next cell's,
-                // or the kPosPad spare entries at the end): masked off below.
-                for (uint32_t j = b; j < e; j += kGroup) {
-                    uint32_t hits = 0;
-                    const float4* pg = pos + j;
-#pragma unroll
-                    for (int u = 0; u < kGroup; ++u) {
-                        const float4 pj = pg[u];
-                        const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
-                        const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                        // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
-                        hits |= (uint32_t)(__float_as_uint(r2) - 1u < r2lim) << u;
-                    }
-                    const uint32_t rem = e - j;
-                    if (rem < (uint32_t)kGroup) hits &= (1u << rem) - 1u;
-                    if (!hits) continue;
-                    nfound += __popc(hits);
-                    const uint32_t nfl = ef > j ? min(ef - j, (uint32_t)kGroup) : 0u;
-                    const uint32_t fm = (uint32_t)((1ull << nfl) - 1ull);
-                    uint32_t hf = hits & fm, hb = hits & ~fm;
-                    while (hf) {
-                        const int u = __ffs(hf) - 1;
-                        hf &= hf - 1u;
-                        if (wf.n + wb.n < max_neibs) wf.put(((j + u) << kCodeBits) | code);
-                    }
-                    while (hb) {
-                        const int u = __ffs(hb) - 1;
-                        hb &= hb - 1u;
-                        if (wf.n + wb.n < max_neibs) wb.put(((j + u) << kCodeBits) | code);
-                    }
-                }
+                // the cell's fluid candidates (to the fluid part), then its boundary candidates
+                // (to the boundary part; fluid i only): each group's hits go to one part
+                scan_part(rb[k], ref[k], wf, bx, by, bz, code);
+                scan_part(ref[k], re[k], wb, bx, by, bz, code);
             }
         }
     }
