@@ -19,7 +19,7 @@
 //     drho_i += 2 xi h c0 sum_j (rho_i - rho_j) F m_j/rho_j = dd_coef (delta_i - delta_j) m_j F / r_j
 //
 // Same structure as the tuned kernels: one thread per particle, split
-// neighbour list read four slots ahead, aF applied once per particle, the
+// neighbour list read four entries (two chunks) ahead, aF applied once per particle, the
 // predictor/corrector epilogue of forces_common.cuh.  The kernel and the
 // viscous model are template parameters; formulation, averaging, diffusion
 // and the skin list are uniform run-time switches.
