@@ -126,8 +126,11 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
 #define SPH_OK_E(e) (((e) >> kCodeBits) < n)
             const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;
             uint32_t k = 0;
+            uint4 qn = make_uint4(0u, 0u, 0u, 0u);
+            if (nf >= 4) qn = __ldg(cp);
             for (; k + 4 <= nf; k += 4, cp += S) {
-                const uint4 q = __ldg(cp);
+                const uint4 q = qn;
+                if (k + 8 <= nf) qn = __ldg(cp + S);  // the next full chunk, one iteration ahead
                 SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
                 SPH_PAIR(false, q.x);
                 SPH_PAIR(false, q.y);
@@ -169,14 +172,24 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
             const float phat_i = phat[i];
             const float pic = sc.pi_coef;
             const Central ci = central_of(pi, cx, cy, cz);
-            // list chunks come from DRAM: two chunks (four entries) in flight per iteration
+            // list chunks come from DRAM: two chunks (four entries) per iteration, loaded one
+            // iteration ahead so that their latency is not on the path to the gathers
             const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;
             uint32_t k = 0;
 // keep a pair of the exact list (COMPACT only)
 #define SPH_KEEP_F(e) if (COMPACT) xf.put(e);
 #define SPH_KEEP_B(e) if (COMPACT) xb.put(e);
+            uint2 an = make_uint2(0u, 0u), bn = make_uint2(0u, 0u);
+            if (nf >= 4) {
+                an = __ldg(lp);
+                bn = __ldg(lp + S);
+            }
             for (; k + 4 <= nf; k += 4, lp += 2 * S) {
-                const uint2 a = __ldg(lp), b = __ldg(lp + S);
+                const uint2 a = an, b = bn;
+                if (k + 8 <= nf) {  // the next iteration's chunks (within the fluid part)
+                    an = __ldg(lp + 2 * S);
+                    bn = __ldg(lp + 3 * S);
+                }
                 SPH_GUARD((max(max(a.x, a.y), max(b.x, b.y)) >> kCodeBits) < n, st, break)
                 if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
                 if (fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
