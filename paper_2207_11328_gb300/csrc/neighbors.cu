@@ -59,7 +59,17 @@ __global__ void __launch_bounds__(kBlock) k_hash(const float4* __restrict__ pos,
                           (uint32_t)sc.ncell[0] * ((uint32_t)nc[1] + (uint32_t)sc.ncell[1] * (uint32_t)nc[2]);
         }
         key[i] = k;
-        slot[i] = atomicAdd(&count[k], 1u);
+        // one atomic per distinct cell of the warp (consecutive particles mostly share
+        // one): the leader reserves the slots of its peers, each takes base + its rank.
+        // The order within a cell is the reorder's to fix, so any slot order will do.
+        const unsigned act = __activemask();
+        const unsigned peers = __match_any_sync(act, k);
+        const int lane = threadIdx.x & 31;
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(&count[k], (uint32_t)__popc(peers));
+        base = __shfl_sync(peers, base, leader);
+        slot[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
     }
 }
 
