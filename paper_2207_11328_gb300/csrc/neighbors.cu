@@ -196,9 +196,11 @@ __global__ void __launch_bounds__(kBlock) k_scatter(const uint32_t* __restrict__
 // Rank each particle of the cell by its unique key (type, id) -> final slot; gather its data from the old arrays, re-base
 // the offset to the new cell (exact: Sterbenz), write the new arrays.
 // ---------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long sort_key(const float4* pos, const uint32_t* pid, uint32_t idx) {
+// (type, id) in 32 bits (ids < kMaxParticles = 2^26): one shuffle per comparison of the rank
+static_assert(kMaxParticles <= (1u << 31), "the id fits below the type bit");
+__device__ __forceinline__ uint32_t sort_key(const float4* pos, const uint32_t* pid, uint32_t idx) {
     const uint32_t bnd = __float_as_uint(pos[idx].w) >> 31;  // sign bit = boundary
-    return ((unsigned long long)bnd << 32) | pid[idx];
+    return (bnd << 31) | pid[idx];
 }
 
 // cells per warp: 4 measured fastest (1.65M dam break, most cells empty: 78 -> 61 us;
@@ -241,21 +243,21 @@ __global__ void __launch_bounds__(kBlock) k_reorder(
             for (uint32_t base = 0; base < n; base += 32) {
                 const uint32_t l = base + lane;
                 uint32_t idx = 0;
-                unsigned long long mine = ~0ull;
+                uint32_t mine = ~0u;  // above every key
                 if (l < n) {
                     idx = unsorted[beg + l];
                     mine = sort_key(pos, pid, idx);
                 }
-                nfluid += __popc(__ballot_sync(0xffffffffu, l < n && (mine >> 32) == 0ull));
+                nfluid += __popc(__ballot_sync(0xffffffffu, l < n && (mine >> 31) == 0u));
                 uint32_t rank = 0;
                 if (n <= 32) {
                     for (uint32_t k = 0; k < n; ++k) {
-                        const unsigned long long o = __shfl_sync(0xffffffffu, mine, (int)k);
+                        const uint32_t o = __shfl_sync(0xffffffffu, mine, (int)k);
                         rank += o < mine;
                     }
                 } else {
                     for (uint32_t k = 0; k < n; ++k) {
-                        const unsigned long long o = sort_key(pos, pid, unsorted[beg + k]);
+                        const uint32_t o = sort_key(pos, pid, unsorted[beg + k]);
                         rank += o < mine;
                     }
                 }
