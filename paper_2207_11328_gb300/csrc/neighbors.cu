@@ -609,8 +609,7 @@ inline unsigned grid_for(uint32_t n, int block) {
 
 uint32_t scan_blocks(uint32_t n_buckets) { return (n_buckets + kScanTile - 1) / kScanTile; }
 
-void launch_hash(const Buffers& b, int cur, const Geometry& g, const Phys& ph, int do_dt, cudaStream_t st) {
-    (void)ph; (void)do_dt;
+void launch_hash(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
     k_hash<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.pos[cur], b.cell[cur], b.pinfo[cur], b.scenes, b.status,
                                                         b.key, b.slot, b.count, g.n_cells, b.gate);
 }
@@ -623,8 +622,7 @@ void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st) {
     k_scan_down<<<blocks, kScanThreads, 0, st>>>(b.count, nb, b.bsum, b.start, b.status, b.gate);
 }
 
-void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
-    (void)cur;
+void launch_scatter(const Buffers& b, const Geometry& g, cudaStream_t st) {
     k_scatter<<<grid_for(g.cap, kBlock), kBlock, 0, st>>>(b.key, b.slot, b.start, b.status, b.unsorted,
                                                            g.n_cells + 1, b.gate);
 }

@@ -351,9 +351,9 @@ int set_scene_table(sph_ctx* c, uint32_t n, const sph_scene* sc) {
 
 // neighbour pipeline on buffer `cur` -> buffer cur^1 (sorted), then list
 void enqueue_sort(sph_ctx* c, cudaStream_t st) {
-    launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+    launch_hash(c->b, c->cur, c->g, st);
     launch_scan(c->b, c->g, st);
-    launch_scatter(c->b, c->cur, c->g, st);
+    launch_scatter(c->b, c->g, st);
     launch_reorder(c->b, c->cur, c->g, st);
     c->cur ^= 1;
 }
@@ -361,9 +361,9 @@ void enqueue_sort(sph_ctx* c, cudaStream_t st) {
 void enqueue_build(sph_ctx* c, cudaStream_t st) {
     if (skin_mode(c)) {
         // gated by status->rebuild; the sorted arrays come back to the same buffer
-        launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+        launch_hash(c->b, c->cur, c->g, st);
         launch_scan(c->b, c->g, st);
-        launch_scatter(c->b, c->cur, c->g, st);
+        launch_scatter(c->b, c->g, st);
         launch_reorder(c->b, c->cur, c->g, st);
         launch_copyback(c->b, c->cur, c->g, st);
         launch_build(c->b, c->cur, c->g, c->ph, st);
@@ -1150,11 +1150,11 @@ int sph_step_profiled(sph_ctx* c, uint32_t nsteps, void* stream, double* phase_m
         cudaEventRecord(ev[0], st);
         launch_dt(c->b, c->g, c->ph, 1, st);
         cudaEventRecord(ev[1], st);
-        launch_hash(c->b, c->cur, c->g, c->ph, 0, st);
+        launch_hash(c->b, c->cur, c->g, st);
         cudaEventRecord(ev[2], st);
         launch_scan(c->b, c->g, st);
         cudaEventRecord(ev[3], st);
-        launch_scatter(c->b, c->cur, c->g, st);
+        launch_scatter(c->b, c->g, st);
         cudaEventRecord(ev[4], st);
         launch_reorder(c->b, c->cur, c->g, st);
         if (skin_mode(c))

@@ -256,9 +256,9 @@ struct Geometry {
 };
 
 // neighbours.cu
-void launch_hash(const Buffers& b, int cur, const Geometry& g, const Phys& ph, int do_dt, cudaStream_t st);
+void launch_hash(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
 void launch_scan(const Buffers& b, const Geometry& g, cudaStream_t st);
-void launch_scatter(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+void launch_scatter(const Buffers& b, const Geometry& g, cudaStream_t st);
 void launch_reorder(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
 void launch_build(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 uint32_t scan_blocks(uint32_t n_buckets);
