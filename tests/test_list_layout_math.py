@@ -34,3 +34,17 @@ def test_chunk_count_is_tight():
     chunks = _list_chunks()
     for m in range(8, 1025, 2):
         assert (1 + 1) // 2 + (m - 1 + 1) // 2 == chunks(m)
+
+
+def test_exact_list_parts_fit():
+    # skin list: the step's exact list in chunks of four, fluid part from chunk 0, boundary
+    # part from chunk exact_bnd_chunk(max_neibs), 2 * exact_bnd_chunk chunks per particle
+    src = open(HEADER).read()
+    m = re.search(r"constexpr uint32_t exact_bnd_chunk\(uint32_t max_neibs\) \{ return ([^;]+); \}", src)
+    assert m, "exact_bnd_chunk not found"
+    expr = m.group(1).replace("u", "").replace("/", "//")
+    kxb = lambda max_neibs: eval(expr, {}, {"max_neibs": max_neibs})  # noqa: E731
+    for mn in range(8, 1025):
+        k = kxb(mn)
+        assert (mn + 3) // 4 <= k          # a fluid part of up to max_neibs entries
+        assert k + (mn + 3) // 4 <= 2 * k  # a boundary part of up to max_neibs entries
