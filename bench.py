@@ -428,6 +428,16 @@ def run_ours(args, world, rank, local):
         nb = st2["builds"] - st1["builds"]
         roofline["profiled_steps"] = {"steps": args.profile_steps, "list_builds": nb,
                                       "build_ms_per_list_build": phases["build"] / max(1, nb)}
+    # the neighbour build, the largest single kernel of an every-step run: its algorithmic
+    # bytes (read pos4 16 + cell 4 + scene 4 per particle, write 4 per entry + the count 4)
+    # against HBM; it is bound by instruction issue (profiles/), not by these bytes
+    nbuilds = max(1, st2["builds"] - st1["builds"]) if skin_mode else args.profile_steps
+    b_build = n * 28 + 4 * e_step
+    t_build = phases["build"] / nbuilds / 1e3
+    roofline["build"] = {"kernel": "neighbour build (" + tuned["build"] + ")", "bound": "issue",
+                         "achieved": b_build / t_build / 1e9, "peak": hbm, "unit": "GB/s",
+                         "frac": b_build / t_build / 1e9 / hbm, "algorithmic_bytes_per_launch": b_build,
+                         "ms_per_launch": 1e3 * t_build}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
