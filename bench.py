@@ -5,11 +5,20 @@
 A step is one pass of the whole hot path: neighbour pipeline (hash, sort,
 reorder, cell start/end, split neighbour list), forces at n + predictor,
 forces at the predicted state + corrector, CFL dt.  The default workload is
-the ~1M-fluid-particle 3D dam break (tank 1.6 x 0.67 x 0.6 m, column
-0.4 x 0.67 x 0.3 m, dp = 4.3 mm, 3 layers of dynamic boundary particles,
-1.65M particles in total), synthetic and seeded; its arrays (~1.3 GB with
-the neighbour list) exceed the 126 MB L2, so no flush is needed between
-steps.
+the 3D dam break refined to ~16M fluid particles (tank 1.6 x 0.67 x 0.6 m,
+column 0.4 x 0.67 x 0.3 m, dp = 4.3 mm / 16^(1/3) = 1.71 mm, 3 layers of
+dynamic boundary particles, 20.1M particles in total), synthetic and seeded,
+with the list rebuilt every step; its arrays (~16 GB with the neighbour
+list) exceed the 126 MB L2 many times over, so no flush is needed between
+steps.  `--workload dam1m` runs the ~1M-fluid-particle version (dp 4.3 mm,
+1.65M particles).
+
+The timed region is exactly --steps steps after --warmup steps from the
+initial column at rest; the line also carries the same measurement taken
+after --flow-steps further steps (`flowing`: the column collapsing), the
+per-kernel roofline (the dominant kernel first), the clocks sampled through
+NVML every 10 ms inside the timed region, the end-to-end figure through the
+C ABI with host buffers, and the FP64 oracle on the host cores.
 
 Metric: particle-interactions/s = (neighbour-list entries of each step's
 build x 2 force passes) / time; particle-steps/s is reported beside it.
@@ -54,24 +63,26 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
-def forces_traffic(workload):
-    """Measured DRAM bytes per force launch (mean of the two passes) from the
-    committed ncu summary, or None when the kernel source (forces.cu and
-    forces_common.cuh) changed since the capture."""
+def kernel_traffic(kernel, workload):
+    """Measured DRAM bytes (read + write) per launch of `kernel` on `workload`
+    from a committed ncu summary (profiles/traffic_*.md: lines `kernel:`,
+    `workload:`, `sources:`, `source_sha256:`, `dram_bytes_per_launch:`), or
+    None when no summary matches or a listed source changed since the capture."""
     import glob
     import hashlib
-    h = hashlib.sha256()
-    for f in ("forces.cu", "forces_common.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2207_11328_gb300", "csrc", f), "rb").read())
-    sha = h.hexdigest()
-    for path in glob.glob(os.path.join(ROOT, "profiles", "forces_traffic_*.md")):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "traffic_*.md"))):
         kv = {}
         for line in open(path):
-            if ":" in line and not line.startswith("#"):
+            if ":" in line and not line.startswith(("#", "|", " ", "`")):
                 k, v = line.split(":", 1)
-                kv[k.strip()] = v.strip()
-        if kv.get("workload") == workload and kv.get("source_sha256") == sha:
-            return 0.5 * (float(kv["predictor_dram_bytes"]) + float(kv["corrector_dram_bytes"]))
+                kv.setdefault(k.strip(), v.strip())
+        if kv.get("kernel") != kernel or kv.get("workload") != workload:
+            continue
+        h = hashlib.sha256()
+        for f in kv.get("sources", "").split(","):
+            h.update(open(os.path.join(ROOT, "paper_2207_11328_gb300", "csrc", f.strip()), "rb").read())
+        if kv.get("source_sha256") == h.hexdigest():
+            return float(kv["dram_bytes_per_launch"])
     return None
 
 
@@ -111,29 +122,111 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+class _Nvml:
+    """The few NVML queries the clock record needs, through ctypes (libnvidia-ml
+    ships with the driver; no Python NVML package is assumed).  Read-only."""
+    SM = 1  # NVML_CLOCK_SM
+    REASONS = {0x8: "hw_slowdown", 0x40: "hw_thermal_slowdown", 0x20: "sw_thermal_slowdown",
+               0x4: "sw_power_cap", 0x80: "hw_power_brake_slowdown"}
+
+    def __init__(self, local_index):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            u = getattr(torch.cuda.get_device_properties(local_index), "uuid", None)
+            uuid = ("GPU-" + str(u)) if u is not None else None
+        except Exception:
+            uuid = None
+        rc = -1
+        if uuid:
+            rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev))
+        if rc != 0:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+            ids = [v for v in vis.split(",") if v.strip()]
+            idx = int(ids[local_index]) if ids and ids[local_index].strip().isdigit() else local_index
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(idx), ctypes.byref(self.dev))
+        if rc != 0:
+            raise OSError("no NVML handle for the device")
+        fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+        self.reasons_fn = fn or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        mx = ctypes.c_uint()
+        self.max_sm = float(mx.value) if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, self.SM,
+                                                                             ctypes.byref(mx)) == 0 else None
+
+    def sample(self):
+        c = self.c
+        sm, pw, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        ok = self.lib.nvmlDeviceGetClockInfo(self.dev, self.SM, c.byref(sm)) == 0
+        self.lib.nvmlDeviceGetPowerUsage(self.dev, c.byref(pw))
+        self.reasons_fn(self.dev, c.byref(rs))
+        return (float(sm.value) if ok else None), pw.value / 1e3, int(rs.value)
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """SM clock, power and throttle reasons sampled every 10 ms (NVML) while the
+    timed region runs; mark() brackets the region and summary() keeps only the
+    samples taken inside it.  Falls back to nvidia-smi at 200 ms without NVML."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.010
 
     def __init__(self, index):
         self.index = index
         self.proc = None
+        self.nvml = None
+        self.rows = []          # (t, sm_mhz, power_w, reasons bits)
+        self.t0 = self.t1 = None
+        self.out = ""
+
+    def _loop(self):
+        while not self._stop.is_set():
+            t = time.perf_counter()
+            try:
+                self.rows.append((t,) + self.nvml.sample())
+            except Exception:
+                pass
+            self._stop.wait(self.PERIOD_S)
 
     def __enter__(self):
+        import threading
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.nvml = _Nvml(self.index)
         except Exception:
-            self.proc = None
-        time.sleep(0.3)
+            self.nvml = None
+        if self.nvml is not None:
+            self._stop = threading.Event()
+            self._th = threading.Thread(target=self._loop, daemon=True)
+            self._th.start()
+        else:
+            try:
+                self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                              "--format=csv,noheader,nounits", "-lms", "200"],
+                                             stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            except Exception:
+                self.proc = None
+            time.sleep(0.3)
         return self
 
+    def mark(self, start):
+        """Host time at the start (start=True, after the synchronize before the
+        region) or the end (after the synchronize that closes it)."""
+        if start:
+            self.t0 = time.perf_counter()
+        else:
+            self.t1 = time.perf_counter()
+
     def __exit__(self, *a):
-        self.out = ""
-        if self.proc:
+        if self.nvml is not None:
+            self._stop.set()
+            self._th.join(timeout=5)
+        elif self.proc:
             time.sleep(0.25)
             self.proc.terminate()
             try:
@@ -143,6 +236,17 @@ class ClockSampler:
         return False
 
     def summary(self):
+        if self.nvml is not None:
+            inside = [r for r in self.rows if self.t0 is not None and self.t1 is not None and self.t0 <= r[0] <= self.t1]
+            sm = [r[1] for r in inside if r[1] is not None]
+            bits = 0
+            for r in inside:
+                bits |= r[3]
+            reasons = sorted(name for b, name in _Nvml.REASONS.items() if bits & b)
+            return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": self.nvml.max_sm,
+                    "sm_mhz_min": min(sm) if sm else None, "power_w_max": max((r[2] for r in inside), default=None),
+                    "reasons": reasons, "samples": len(inside), "source": "NVML every 10 ms inside the timed region",
+                    "region_s": (self.t1 - self.t0) if self.t0 is not None and self.t1 is not None else None}
         rows = [r for r in csv.reader(io.StringIO(self.out or "")) if len(r) >= 9]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
@@ -152,7 +256,7 @@ class ClockSampler:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
         load = sorted(sm)[len(sm) // 2:] if sm else []   # upper half: samples under load
         return {"sm_mhz": float(np.median(load)) if load else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": "nvidia-smi every 200 ms around the region"}
 
 
 def dist_setup(n_gpus):
@@ -337,6 +441,52 @@ def run_reference(args, world, rank):
 
 
 # ---------------------------------------------------------------------------
+# Algorithmic bytes per launch of each kernel of a step (what the method must move;
+# neighbour candidates and gathers are served by L1/L2/shared memory by construction of
+# the cell sort), with n particles and e list entries of the step's build:
+#   hash      read pos4 16 + cell 4 + scene 4, write key 4 + slot 4              32 n
+#   reorder   read unsorted 4 + pos4 16 + vel4 16 + P/rho^2 4 + scene 4 + id 4,
+#             write the same five arrays + cell 4                                96 n
+#   build     read pos4 16 + cell 4 + scene 4, write count 4 + list 4 e           28 n + 4 e
+#   forces + predictor   read pos4 16 + vel4 16 + scene 4 + count 4 + list 4 e,
+#                        write pos*, vel* 32                                      72 n + 4 e
+#   forces + corrector   the same reads at the predicted state, read and write
+#                        the state n (64)                                         104 n + 4 e
+#   build + forces + predictor (one kernel)  read pos4 16 + vel4 16 + cell 4 + scene 4,
+#                        write count 4 + list 4 e + pos*, vel* 32 + P*/rho*^2 4   80 n + 4 e
+def algorithmic_bytes(phase, n, e):
+    return {"hash": 32 * n, "reorder": 96 * n, "build": 28 * n + 4 * e, "forces_predict": 72 * n + 4 * e,
+            "forces_correct": 104 * n + 4 * e, "build_predict": 80 * n + 4 * e}.get(phase)
+
+
+KERNEL_NAMES = {"build": "k_build_tpp", "forces_predict": "k_forces<predictor>",
+                "forces_correct": "k_forces<corrector>", "reorder": "k_reorder", "hash": "k_hash",
+                "build_predict": "k_tile_predict"}
+
+
+def timed_region(sim, steps, stream, world, local):
+    """Exactly `steps` steps between CUDA events on the launch stream, bracketed
+    by a barrier and a synchronize on both sides; clocks sampled inside.
+    Returns (ms, stats before, stats after, clock summary)."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    st0 = sim.stats(stream=stream)
+    with ClockSampler(local) as clk:
+        barrier(world)
+        torch.cuda.synchronize()
+        clk.mark(True)
+        ev0.record(stream)
+        sim.step(steps, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk.mark(False)
+        barrier(world)
+    ms = ev0.elapsed_time(ev1)
+    st1 = sim.stats(stream=stream)
+    return ms, st0, st1, clk.summary()
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_2207_11328_gb300 import Simulation, _build, fp32_peak
@@ -363,24 +513,15 @@ def run_ours(args, world, rank, local):
         sim.autotune(stream=stream)
     tuned = sim.variants()
     sim.step(args.warmup, stream=stream)
-    torch.cuda.synchronize()
-    st0 = sim.stats(stream=stream)
 
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier(world)
-        torch.cuda.synchronize()
-        ev0.record(stream)
-        sim.step(args.steps, stream=stream)
-        ev1.record(stream)
-        torch.cuda.synchronize()
-        barrier(world)
-    ms = ev0.elapsed_time(ev1)
-    st1 = sim.stats(stream=stream)
-    # interactions: 2 force passes x pairs within 2h (the list itself when it is rebuilt every
-    # step; counted by the first force pass when the list carries a skin)
-    entries = (st1["interactions"] - st0["interactions"]) if skin_mode else (st1["list_entries"] - st0["list_entries"])
-    inter_local = 2.0 * entries
+    def pairs_of(st0, st1):
+        # interactions: 2 force passes x pairs within 2h (the list itself when it is rebuilt
+        # every step; counted by the first force pass when the list carries a skin)
+        return 2.0 * ((st1["interactions"] - st0["interactions"]) if skin_mode
+                      else (st1["list_entries"] - st0["list_entries"]))
+
+    ms, st0, st1, clocks = timed_region(sim, args.steps, stream, world, local)
+    inter_local = pairs_of(st0, st1)
     psteps_local = float(st1["n_active"]) * args.steps
     value, psteps, t_max = aggregate(world, inter_local, psteps_local, ms / 1e3)
     kernels = st1["kernels_per_step"]
@@ -389,55 +530,53 @@ def run_ours(args, world, rank, local):
     phases = sim.step_profiled(args.profile_steps, stream=stream)
     st2 = sim.stats(stream=stream)
     n = float(st2["n_active"])
+    nbuilds = max(1, st2["builds"] - st1["builds"]) if skin_mode else args.profile_steps
     # list entries read per force launch: the list of the step (rebuilt every step), or the
     # skin list (its entries per build, read by every step until the next build)
     e_step = (st2["list_entries"] - st1["list_entries"]) / max(1, st2["builds"] - st1["builds"])
     hbm, peak_src = load_peaks()
-    # algorithmic bytes per launch (neighbour gathers served by L1/L2 by construction of the sort):
-    #   forces+predictor: read pos4 16 + vel4 16 + scene 4 + count 4 + list 4/entry; write pos*, vel* 32
-    #   forces+corrector: the same reads of the predicted state + list, read and write pos4, vel4 (64)
-    b_pred = n * 72 + 4 * e_step
-    b_corr = n * 104 + 4 * e_step
-    pairs_step = 2 * e_step  # pair terms evaluated by the two passes
-    if skin_mode:
-        # the predictor reads the skin list and writes the step's exact list (+ its counts),
-        # the corrector reads the exact list; pairs within 2h per pass from the counter
-        e_exact = (st2["interactions"] - st1["interactions"]) / args.profile_steps
-        b_pred = n * 76 + 4 * e_step + 4 * e_exact
-        b_corr = n * 104 + 4 * e_exact
-        pairs_step = 2 * e_exact
-    t_pred = phases["forces_predict"] / args.profile_steps / 1e3
-    t_corr = phases["forces_correct"] / args.profile_steps / 1e3
-    achieved = (b_pred + b_corr) / (t_pred + t_corr) / 1e9
-    traffic = forces_traffic(args.workload) if not skin_mode else None
-    # the ALU roof: FP32 flops of a pair term (FMA = 2): separation 3, r^2 5, r 2, q - 2 2,
-    # m (q-2)^3 3, u_ij 3, u.x 5, continuity 2, pressure bracket 1, coefficient 1, a 6 = 33
-    # (+9 on approaching pairs for the artificial viscosity, not counted), per pair evaluated
+    launches = {p: (nbuilds if p in ("hash", "scan", "scatter", "reorder", "build") and skin_mode
+                    else args.profile_steps) for p in phases}
+    per_launch_ms = {p: phases[p] / max(1, launches[p]) for p in phases if phases[p] > 0}
+    step_ms = {p: phases[p] / args.profile_steps for p in phases}
+    kernels_rf = {}
+    for p in ("build_predict", "build", "forces_predict", "forces_correct", "reorder", "hash"):
+        if p not in per_launch_ms:
+            continue
+        e_p = e_step
+        if skin_mode and p in ("forces_correct",):
+            e_p = (st2["interactions"] - st1["interactions"]) / args.profile_steps
+        byts = algorithmic_bytes(p, n, e_p)
+        if skin_mode and p == "forces_predict":  # reads the skin list, writes the exact list and counts
+            byts = 76 * n + 4 * e_step + 4 * (st2["interactions"] - st1["interactions"]) / args.profile_steps
+        t = per_launch_ms[p] / 1e3
+        kernels_rf[p] = {"kernel": KERNEL_NAMES.get(p, p), "achieved": byts / t / 1e9, "unit": "GB/s",
+                         "frac": byts / t / 1e9 / hbm, "algorithmic_bytes_per_launch": byts,
+                         "ms_per_launch": 1e3 * t, "share_of_step": step_ms[p] / max(1e-12, sum(step_ms.values())),
+                         "traffic": None if skin_mode else kernel_traffic(KERNEL_NAMES.get(p, p), args.workload)}
+    dom = max(kernels_rf, key=lambda p: kernels_rf[p]["share_of_step"])
+    d = kernels_rf[dom]
+    roofline = {"bound": "hbm", "kernel": d["kernel"], "achieved": d["achieved"], "peak": hbm,
+                "peak_source": f"{peak_src} HBM copy bandwidth (of {peak_src})", "unit": "GB/s",
+                "frac": d["frac"], "traffic": d["traffic"],
+                "algorithmic_bytes_per_launch": d["algorithmic_bytes_per_launch"], "ms_per_launch": d["ms_per_launch"],
+                "note": "dominant kernel by share of the step; it is bound by instruction issue, not by HBM "
+                        "(see kernels[*] and the ncu summaries)",
+                "kernels": kernels_rf, "phase_ms_per_step": step_ms}
+    # the ALU view of the force passes: FP32 flops of a pair term (FMA = 2): separation 3,
+    # r^2 5, r 2, q - 2 2, m (q-2)^3 3, u_ij 3, u.x 5, continuity 2, pressure bracket 1,
+    # coefficient 1, a 6 = 33 (+9 on approaching pairs for the artificial viscosity, not counted)
+    pairs_step = 2 * ((st2["interactions"] - st1["interactions"]) / args.profile_steps if skin_mode else e_step)
+    t_forces = (phases.get("forces_predict", 0.0) + phases.get("forces_correct", 0.0)
+                + phases.get("build_predict", 0.0)) / args.profile_steps / 1e3
     alu_peak = fp32_peak(stream)
-    alu = 33.0 * pairs_step / (t_pred + t_corr) / 1e12
-    roofline = {"bound": "hbm", "kernel": "forces (predictor + corrector passes)", "achieved": achieved,
-                "peak": hbm, "peak_source": f"{peak_src} HBM copy bandwidth", "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": traffic,
-                "algorithmic_bytes_per_launch": 0.5 * (b_pred + b_corr),
-                "algorithmic_bytes_per_step": b_pred + b_corr,
-                "alu": {"achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu / alu_peak,
-                        "peak_source": "measured FP32 FMA throughput (sph_fp32_peak)",
-                        "flops_per_pair": 33},
-                "phase_ms_per_step": {k: v / args.profile_steps for k, v in phases.items()}}
+    alu = 33.0 * pairs_step / max(t_forces, 1e-12) / 1e12
+    roofline["alu"] = {"kernel": "force passes", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s",
+                       "frac": alu / alu_peak, "peak_source": "measured FP32 FMA throughput (sph_fp32_peak)",
+                       "flops_per_pair": 33}
     if skin_mode:
-        nb = st2["builds"] - st1["builds"]
-        roofline["profiled_steps"] = {"steps": args.profile_steps, "list_builds": nb,
-                                      "build_ms_per_list_build": phases["build"] / max(1, nb)}
-    # the neighbour build, the largest single kernel of an every-step run: its algorithmic
-    # bytes (read pos4 16 + cell 4 + scene 4 per particle, write 4 per entry + the count 4)
-    # against HBM; it is bound by instruction issue (profiles/), not by these bytes
-    nbuilds = max(1, st2["builds"] - st1["builds"]) if skin_mode else args.profile_steps
-    b_build = n * 28 + 4 * e_step
-    t_build = phases["build"] / nbuilds / 1e3
-    roofline["build"] = {"kernel": "neighbour build (" + tuned["build"] + ")", "bound": "issue",
-                         "achieved": b_build / t_build / 1e9, "peak": hbm, "unit": "GB/s",
-                         "frac": b_build / t_build / 1e9 / hbm, "algorithmic_bytes_per_launch": b_build,
-                         "ms_per_launch": 1e3 * t_build}
+        roofline["profiled_steps"] = {"steps": args.profile_steps, "list_builds": nbuilds,
+                                      "build_ms_per_list_build": phases["build"] / nbuilds}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
@@ -447,12 +586,28 @@ def run_ours(args, world, rank, local):
                        "physics": physics,
                        "rebuild": "every step" if not skin_mode else
                                   f"every {args.rebuild_every} steps, list radius 2h + {args.skin}h",
+                       "state": f"initial column at rest after {args.warmup} warm-up steps",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
                        "variants": dict(tuned, autotuned=not args.variants)},
-            "particle_steps_per_s": psteps, "mean_neighbours": entries / max(1.0, psteps_local),
+            "particle_steps_per_s": psteps, "mean_neighbours": inter_local / 2 / max(1.0, psteps_local),
             "list_builds": st1["builds"] - st0["builds"],
             "roofline": roofline, "gpu_launches": int(kernels * args.steps),
-            "clocks": clk.summary()}
+            "clocks": clocks}
+    line["clocks"]["time_x_median_mhz"] = (1e3 * t_max / args.steps * clocks["sm_mhz"]
+                                           if clocks.get("sm_mhz") else None)
+
+    # the same measurement on a flowing state: the column collapses for flow_steps more steps
+    if args.flow_steps > 0:
+        sim.step(args.flow_steps, stream=stream)
+        ms_f, sf0, sf1, clk_f = timed_region(sim, args.steps, stream, world, local)
+        inter_f = pairs_of(sf0, sf1)
+        ps_f = float(sf1["n_active"]) * args.steps
+        v_f, p_f, t_f = aggregate(world, inter_f, ps_f, ms_f / 1e3)
+        line["flowing"] = {"value": v_f, "unit": UNIT, "ms_per_step": 1e3 * t_f / args.steps,
+                           "particle_steps_per_s": p_f, "steps": args.steps,
+                           "steps_before": args.warmup + args.steps + args.profile_steps + args.flow_steps,
+                           "simulated_time_s": sf1["time"], "mean_neighbours": inter_f / 2 / max(1.0, ps_f),
+                           "n_removed": sf1["n_removed"], "clocks": clk_f}
 
     # end to end through the public API with host buffers (upload, one step, download)
     if args.e2e_steps > 0:
@@ -590,9 +745,12 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="dam1m", choices=["dam1m", "dam16m", "box", "box2m", "batch", "adjoint"])
+    ap.add_argument("--workload", default="dam16m", choices=["dam1m", "dam16m", "box", "box2m", "batch", "adjoint"])
     ap.add_argument("--max-neibs", type=int, default=128)
-    ap.add_argument("--profile-steps", type=int, default=50)
+    ap.add_argument("--profile-steps", type=int, default=20)
+    ap.add_argument("--flow-steps", type=int, default=2000,
+                    help="steps taken after the timed region before timing --steps again on the flowing state "
+                         "(0: skip)")
     ap.add_argument("--variants", default="",
                     help="build,predictor,corrector variant indices (0..4) instead of autotuning")
     ap.add_argument("--e2e-steps", type=int, default=20)

@@ -105,7 +105,8 @@ typedef struct {
     double   alpha;          /* artificial-viscosity coefficient */
     double   nu;             /* kinematic viscosity (laminar) */
     double   g[3];           /* body force per unit mass on fluid particles */
-    double   cfl;            /* CFL factor of the adaptive time step */
+    double   cfl;            /* CFL factor of the adaptive time step: dt = min(cfl*min(sqrt(h/|a|max), h/c0),
+                                0.125 h^2/nu [laminar models]) */
     double   dt_fixed;       /* > 0: constant time step; <= 0: adaptive (CFL) */
     double   origin[3];      /* domain of scene 0 */
     double   size[3];
@@ -210,7 +211,16 @@ int sph_forces(sph_ctx* ctx, void* stream);
 
 /* nsteps predictor-corrector steps, each: neighbour pipeline, forces at n,
  * predictor (dt/2), forces at the predicted state, corrector (dt), CFL dt
- * for the next step.  Replays a captured CUDA graph per step. */
+ * for the next step.  Paper: Section 2.1 (the method), Section 3 "Code
+ * structure" (the integrator runs forces and euler twice per step, the
+ * first stage over dt/2, the second over dt) and Section 3 "The GPU in
+ * GPUSPH" (the time step is a minimum over particles by parallel reduction);
+ * the update formulas are reading C6, the dt formula reading C7 (not
+ * printed in the paper).  Replays a captured CUDA graph per step: no host
+ * round trip, the counters GPUSPH downloads every step stay on the device
+ * until sph_get_stats.  Errors: SPH_ERR_STATE before an upload,
+ * SPH_ERR_CUDA on a launch failure; device-found errors are sticky (see
+ * Conventions). */
 int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
 
 /* ---- differentiable run (reverse mode) --------------------------------
@@ -245,6 +255,16 @@ int sph_record(sph_ctx* ctx, uint32_t T, uint32_t K, void* stream, double* dt_ou
  * context at the recorded initial state.  Synchronises `stream`. */
 int sph_backward(sph_ctx* ctx, const float* xbar_T, const float* ubar_T, const float* dbar_T, float* xbar_0,
                  float* ubar_0, float* dbar_0, double* alphabar, void* stream);
+
+/* Generation of the recording sph_backward would reverse: every successful
+ * sph_record numbers its tape 1, 2, 3, ... per context; *gen = 0 when no
+ * valid recording exists (none yet, a failed sph_record, sph_set_alpha).
+ * A caller that holds several recordings' results (e.g. an autograd graph
+ * with two rollouts on one context) stores the generation after its
+ * sph_record and checks it before sph_backward: a mismatch means the tape
+ * now belongs to a later recording.  The paper has no counterpart.  Host
+ * call, no synchronisation; SPH_ERR_ARG for a null argument. */
+int sph_tape_generation(sph_ctx* ctx, uint64_t* gen);
 
 /* Autotuner (launch shapes only; results are unchanged): times each
  * neighbour-build variant (one thread per particle with 128 or 256 threads
@@ -290,8 +310,13 @@ const char* sph_forces_variant_name(int variant);
 int sph_step_profiled(sph_ctx* ctx, uint32_t nsteps, void* stream, double* phase_ms);
 
 /* Download the state in upload order into HOST arrays (any may be NULL):
- * pos n*3 FP64, vel n*3 FP32, delta n FP32.  Particles removed from the
- * domain read as NaN.  n must equal the uploaded count.  Synchronises. */
+ * pos n*3 FP64, vel n*3 FP32, delta n FP32.  Paper: Section 3 "The GPU in
+ * GPUSPH" (particle data is downloaded to the host only at fixed simulated
+ * time intervals, with the simulation suspended meanwhile): a host call
+ * between steps, never inside one.  Particles removed from the domain read
+ * as NaN.  n must equal the uploaded count (else SPH_ERR_ARG).
+ * Synchronises `stream`; returns the sticky device error as sph_get_stats
+ * does. */
 int sph_download(sph_ctx* ctx, uint32_t n, double* pos, float* vel, float* delta, void* stream);
 
 /* Same as sph_download into DEVICE arrays (no host synchronisation). */
@@ -331,15 +356,21 @@ int sph_download_neighbors_noalloc(sph_ctx* ctx, uint32_t n, uint32_t* counts, u
  * forces-only pass (its results also land where sph_download_forces reads them):
  *   out[0..2] momentum sum_i m_i u_i (fluid),  out[3..5] force sum_i m_i a_i,
  *   out[6] sum_i m_i drho_i/dt,  out[7] kinetic energy sum_i m_i |u_i|^2 / 2,
+ *   out[8] total mass sum_i m_i (particles in the domain),
  * masses taken positive.  With no boundary particles and no gravity the pair forces
  * cancel: out[3..5] vanish to rounding.  FP64 sums in a fixed order (bitwise
- * reproducible).  HOST out[8]; synchronises `stream`; returns the sticky device
+ * reproducible).  HOST out[9]; synchronises `stream`; returns the sticky device
  * error as sph_get_stats does. */
 int sph_conservation(sph_ctx* ctx, double* out, void* stream);
 
-/* Read device counters into *out (synchronises `stream`).  Returns the
- * sticky device error as a code (SPH_ERR_NEIB_OVERFLOW, SPH_ERR_NONFINITE,
- * SPH_ERR_TIMEOUT) if one is set, else SPH_OK; *out is filled either way. */
+/* Read device counters into *out (synchronises `stream`).  Paper: Section 3
+ * "The GPU in GPUSPH" (the only data that returns to the host between
+ * steps: the particle count after the sort, which shows removed particles,
+ * the largest neighbour count of the list build, which shows an overflow,
+ * and the time step of the reduction).  Returns the sticky device error as
+ * a code (SPH_ERR_NEIB_OVERFLOW, SPH_ERR_NONFINITE, SPH_ERR_SKIN,
+ * SPH_ERR_TIMEOUT) if one is set, else SPH_OK; *out is filled either way.
+ * SPH_ERR_ARG for a null context or output. */
 int sph_get_stats(sph_ctx* ctx, sph_stats* out, void* stream);
 
 /* Per-scene dt and simulated time (n_scenes entries each, HOST, nullable). */
@@ -361,7 +392,14 @@ int sph_fp32_peak(void* stream, double* tflops);
 /* Human-readable text of a return code (static storage). */
 const char* sph_strerror(int code);
 
-/* Free every buffer of the context (synchronises the device). */
+/* Free every buffer of the context (synchronises the device).  Paper:
+ * Section 3 "The GPU in GPUSPH" (arrays are allocated once, at
+ * initialisation, and never reallocated while the simulation runs): the
+ * buffers sph_create allocated live until this call; apart from them only
+ * sph_set_scenes (the cell tables of a new scene table), sph_record (its
+ * tape) and sph_download_neighbors (per-call staging) allocate device
+ * memory.  A null context is ignored.  The context must not be used
+ * afterwards; work still queued on its streams is waited for first. */
 void sph_destroy(sph_ctx* ctx);
 
 #ifdef __cplusplus

@@ -8,8 +8,11 @@
  * It is written to be checked against the paper by eye: plain loops, FP64,
  * no blocking or fusion.  Every function cites the passage it follows
  * (arXiv 2207.11328, "Fast, feature-rich weakly-compressible SPH on GPU").
- * Where the paper only cites another work or is garbled, the reading used is
- * stated beside the code (readings C1..C9 of the design notes).
+ * Where the paper only cites another work, leaves a symbol undefined or
+ * prints a sign or a factor that cannot be right, the reading taken is
+ * stated in full beside the formula it affects, with the passage it reads
+ * (e.g. the continuity sign of Eq. mass-cont-sph1, the missing m_j of
+ * Eq. ns-sph1, the artificial viscosity that Table 1 only names).
  *
  * Scalar type: every formula is a template on the scalar so that the same
  * code runs in double and in forward-mode dual numbers (directional
@@ -449,9 +452,17 @@ void rhs_all(const ora_params& P, int n, const T* x, const T* u, const T* delta,
                      N.idx.data() + N.off[i], N.off[i + 1] - N.off[i], a + 3 * i, drho + i);
 }
 
-/* CFL time step (reading C7): dt = cfl * min(min_i sqrt(h/|a_i|) over fluid,
- * h/c0, h^2/nu for laminar viscosity).  Table 1 "adaptive time-stepping";
- * Section "The GPU in GPUSPH": the minimum is a reduction over particles. */
+/* CFL time step (reading C7): dt = min(cfl * min(min_i sqrt(h/|a_i|) over
+ * fluid, h/c0), 0.125 h^2/nu for laminar viscosity).  Table 1 "adaptive
+ * time-stepping"; Section "The GPU in GPUSPH": the minimum is a reduction over
+ * particles.  The viscous limit carries its own coefficient, not the CFL
+ * factor: the laminar term's fastest mode on the lattice (neighbours of odd
+ * parity moving against the particle) decays at lambda ~ 7 nu/h^2 at
+ * h = 1.3 dp, and the two-stage predictor-corrector is stable for a real
+ * negative eigenvalue only while lambda dt <= 2; 0.125 h^2/nu (the explicit
+ * viscous-diffusion limit usual for SPH) keeps lambda dt below 1. */
+constexpr double kViscousDtCoef = 0.125;
+
 double cfl_dt(const ora_params& P, int n, const double* a, const uint8_t* type) {
     double amax2 = 0.0;
     for (int i = 0; i < n; ++i) {
@@ -461,8 +472,9 @@ double cfl_dt(const ora_params& P, int n, const double* a, const uint8_t* type) 
     }
     double dt = P.h / P.c0;
     if (amax2 > 0.0) dt = std::min(dt, std::sqrt(P.h / std::sqrt(amax2)));
-    if (P.visc_model >= 1 && P.nu > 0.0) dt = std::min(dt, P.h * P.h / P.nu);
-    return P.cfl * dt;
+    dt *= P.cfl;
+    if (P.visc_model >= 1 && P.nu > 0.0) dt = std::min(dt, kViscousDtCoef * P.h * P.h / P.nu);
+    return dt;
 }
 
 void wrap_positions(const ora_params& P, int n, double* x) {

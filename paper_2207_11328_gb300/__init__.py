@@ -95,6 +95,7 @@ _SIGS = {
     "sph_set_alpha": [_vp, ctypes.c_double],
     "sph_record": [_vp, ctypes.c_uint32, ctypes.c_uint32, _vp, _vp],
     "sph_backward": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp],
+    "sph_tape_generation": [_vp, _vp],
     "sph_set_variants": [_vp, ctypes.c_int, ctypes.c_int],
     "sph_build_variant_name": [ctypes.c_int],
     "sph_forces_variant_name": [ctypes.c_int],
@@ -325,10 +326,11 @@ class Simulation:
         return _lib().sph_build_variant_name(v.value).decode(), _lib().sph_forces_variant_name(fv.value).decode()
 
     def conservation(self, stream=None):
-        """Momentum (3), force sum m a (3), sum m drho/dt, kinetic energy at the current state."""
-        out = np.zeros(8, np.float64)
+        """Momentum (3), force sum m a (3), sum m drho/dt, kinetic energy and total mass at the
+        current state."""
+        out = np.zeros(9, np.float64)
         _check(_lib().sph_conservation(self._h, _ptr(out), _stream_handle(stream)), "sph_conservation")
-        return {"momentum": out[0:3], "force": out[3:6], "mass_rate": out[6], "kinetic": out[7]}
+        return {"momentum": out[0:3], "force": out[3:6], "mass_rate": out[6], "kinetic": out[7], "mass": out[8]}
 
     def set_variants(self, build=-1, forces=-1):
         """Select the build variant and force launch shape of every pass (0..4, -1 keeps)."""
@@ -355,6 +357,12 @@ class Simulation:
         dt = ctypes.c_double()
         _check(_lib().sph_record(self._h, int(T), int(K), _stream_handle(stream), ctypes.byref(dt)), "sph_record")
         return dt.value
+
+    def tape_generation(self):
+        """Generation of the recording the next backward() reverses (0: none)."""
+        g = ctypes.c_uint64()
+        _check(_lib().sph_tape_generation(self._h, ctypes.byref(g)), "sph_tape_generation")
+        return g.value
 
     def backward(self, xbar_T=None, ubar_T=None, dbar_T=None, want_x=False, want_delta=False, stream=None):
         """Adjoint of the last record: torch CUDA float32 inputs (n,3)/(n,) or None;

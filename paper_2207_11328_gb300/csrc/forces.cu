@@ -453,10 +453,10 @@ void launch_forces_v(const Buffers& b, int cur, const Geometry& g, const Phys& p
 }
 
 // Conservation sums (Section 2.1 invariants) over particles: momentum sum m u,
-// force sum m a, sum m drho/dt, kinetic energy; |m| (boundary masses are stored
-// negated).  Deterministic: a fixed grid, a fixed particle order per thread and
+// force sum m a, sum m drho/dt, kinetic energy, total mass; |m| (boundary masses
+// are stored negated).  Deterministic: a fixed grid, a fixed particle order per thread and
 // fixed-order tree reductions in FP64 (per block, then over blocks).
-constexpr int kConsBlocks = 304, kConsThreads = 256, kConsQ = 8;
+constexpr int kConsBlocks = 304, kConsThreads = 256, kConsQ = kConservationSums;
 
 __global__ void __launch_bounds__(kConsThreads) k_cons_partial(const float4* __restrict__ pos,
                                                                const float4* __restrict__ vel,
@@ -464,7 +464,7 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(const float4* __r
                                                                const DevStatus* __restrict__ st,
                                                                double* __restrict__ part) {
     __shared__ double red[kConsQ][kConsThreads];
-    double q[kConsQ] = {0, 0, 0, 0, 0, 0, 0, 0};
+    double q[kConsQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * kConsThreads + threadIdx.x; i < n; i += kConsBlocks * kConsThreads) {
         const double m = fabs((double)pos[i].w);
@@ -479,6 +479,7 @@ __global__ void __launch_bounds__(kConsThreads) k_cons_partial(const float4* __r
         q[5] += m * a.z;
         q[6] += m * a.w;
         q[7] += 0.5 * m * (ux * ux + uy * uy + uz * uz);
+        q[8] += m;
     }
 #pragma unroll
     for (int k = 0; k < kConsQ; ++k) red[k][threadIdx.x] = q[k];

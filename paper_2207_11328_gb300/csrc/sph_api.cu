@@ -16,6 +16,8 @@ using namespace sphg;
 // K steps and a per-step tape of one segment, re-filled during the backward.
 struct AdjTape {
     bool valid = false;
+    uint64_t gen = 0;          // generation of the valid recording (0: none)
+    uint64_t next_gen = 1;     // the next sph_record's generation
     uint32_t T = 0, K = 0, n = 0;
     double dt = 0.0;
     Phys ph_rec{};
@@ -102,6 +104,8 @@ void check_canaries(sph_ctx* c, cudaStream_t st) {
     } while (0)
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+constexpr double kViscousDtCoef = 0.125;  // laminar viscous time-step limit, dt <= 0.125 h^2/nu
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -283,9 +287,12 @@ int scene_from(const sph_params& p, const double origin[3], const double size[3]
     s.pi_coef = (float)(p.alpha * p.h * c0 / p.rho0);
     s.pi_unit = (float)(p.h * c0 / p.rho0);
     s.dd_coef = (float)(2.0 * p.ddiff_coef * p.h * c0);
-    double cap = p.h / c0;
-    if (p.visc_model != SPH_VISC_ARTIFICIAL && p.nu > 0.0) cap = std::fmin(cap, p.h * p.h / p.nu);
-    s.dt_cap = p.cfl * cap;
+    // reading C7: cfl * h/c0, and for laminar viscosity 0.125 h^2/nu, a limit with its own
+    // coefficient (the lattice's fastest viscous mode decays at ~7 nu/h^2 at h = 1.3 dp and
+    // the two-stage predictor-corrector is stable while that rate times dt stays <= 2)
+    double cap = p.cfl * p.h / c0;
+    if (p.visc_model != SPH_VISC_ARTIFICIAL && p.nu > 0.0) cap = std::fmin(cap, kViscousDtCoef * p.h * p.h / p.nu);
+    s.dt_cap = cap;
     return SPH_OK;
 }
 
@@ -681,8 +688,8 @@ int sph_conservation(sph_ctx* c, double* out, void* stream) {
     double* scratch = (double*)c->b.staging;
     launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 0, st);
     launch_conservation(c->b, c->cur, scratch, st);
-    CK(cudaMemcpyAsync(out, (char*)scratch + bytes - 8 * sizeof(double), 8 * sizeof(double), cudaMemcpyDeviceToHost,
-                       st));
+    CK(cudaMemcpyAsync(out, (char*)scratch + bytes - kConservationSums * sizeof(double),
+                       kConservationSums * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     DevStatus hs;
     CK(cudaMemcpy(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost));
@@ -883,6 +890,7 @@ void free_tape(sph_ctx* c) {
                 gs[k] = nullptr;
             }
     t.valid = false;
+    t.gen = 0;
 }
 
 // copy the particle arrays of buffer `cur` to / from a flat device block
@@ -971,6 +979,7 @@ int sph_set_alpha(sph_ctx* c, double alpha) {
     CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->scenes_h.size(), cudaMemcpyHostToDevice));
     drop_graphs(c);
     c->tape.valid = false;
+    c->tape.gen = 0;
     return SPH_OK;
 }
 
@@ -1021,6 +1030,7 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     cudaStream_t st = S(stream);
     AdjTape& t = c->tape;
     t.valid = false;
+    t.gen = 0;
     DevStatus hs;
     CK(cudaMemcpyAsync(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -1083,9 +1093,16 @@ int sph_record(sph_ctx* c, uint32_t T, uint32_t K, void* stream, double* dt_out)
     enqueue_build(c, st);
     CK(cudaStreamSynchronize(st));
     t.valid = true;
+    t.gen = t.next_gen++;
     c->need_dt0 = true;
     c->fresh = true;
     if (dt_out) *dt_out = dt;
+    return SPH_OK;
+}
+
+int sph_tape_generation(sph_ctx* c, uint64_t* gen) {
+    if (!c || !gen) return SPH_ERR_ARG;
+    *gen = c->tape.valid ? c->tape.gen : 0u;
     return SPH_OK;
 }
 
@@ -1255,17 +1272,26 @@ int sph_download_neighbors(sph_ctx* c, uint32_t n, uint32_t* counts, uint32_t* i
         cudaFree(dcnt);
         return SPH_ERR_CUDA;
     }
-    cudaMemsetAsync(dcnt, 0, sizeof(uint32_t) * 2 * n, st);
-    cudaMemsetAsync(dids, 0xFF, sizeof(uint32_t) * nid, st);
-    k_download_neighbors<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.nlist, c->b.ncount, c->b.pid[c->cur],
-                                                                   c->b.status, n, c->p.max_neibs, c->ph.stride, dcnt,
-                                                                   dids);
-    cudaMemcpyAsync(counts, dcnt, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, st);
-    cudaMemcpyAsync(ids, dids, sizeof(uint32_t) * nid, cudaMemcpyDeviceToHost, st);
-    cudaError_t e = cudaStreamSynchronize(st);
+    // every step checked; on a failure the staging is freed after the stream drains
+    cudaError_t e = cudaMemsetAsync(dcnt, 0, sizeof(uint32_t) * 2 * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dids, 0xFF, sizeof(uint32_t) * nid, st);
+    if (e == cudaSuccess) {
+        k_download_neighbors<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.nlist, c->b.ncount, c->b.pid[c->cur],
+                                                                       c->b.status, n, c->p.max_neibs, c->ph.stride,
+                                                                       dcnt, dids);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dcnt, sizeof(uint32_t) * 2 * n, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ids, dids, sizeof(uint32_t) * nid, cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
     cudaFree(dcnt);
     cudaFree(dids);
-    return e == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "sph: sph_download_neighbors failed: %s\n", cudaGetErrorString(e));
+        return SPH_ERR_CUDA;
+    }
+    return SPH_OK;
 }
 
 // ---------------------------------------------------------------------

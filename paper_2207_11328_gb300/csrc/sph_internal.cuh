@@ -300,8 +300,9 @@ void launch_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph,
 void launch_forces_models(const Buffers& b, int cur, const Geometry& g, const Phys& ph, ForceMode mode,
                           int acc_dt, cudaStream_t st);
 void launch_copyback(const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
-// conservation sums of the state in buffer cur and the forces in b.force (8 doubles at
-// scratch + 8 * 304, after 304 * 8 doubles of block partials)
+// conservation sums of the state in buffer cur and the forces in b.force
+// (kConservationSums doubles at the end of the scratch, after the block partials)
+constexpr int kConservationSums = 9;
 size_t conservation_scratch_bytes();
 void launch_conservation(const Buffers& b, int cur, double* scratch, cudaStream_t st);
 void launch_force_rebuild(const Buffers& b, cudaStream_t st);

@@ -106,3 +106,36 @@ def oracle_params_kw(scene, **kw):
              visc_avg=scene.visc_avg, ddiff=scene.ddiff, ddiff_coef=scene.ddiff_coef, zeta=scene.zeta)
     d.update(kw)
     return d
+
+
+def compare_neighbor_sets_sample(scene, sample, counts, ids, band=1e-6):
+    """compare_neighbor_sets restricted to the particles in `sample` (the
+    oracle's sets of all particles are computed, those of the sample
+    compared).  Returns the number of compared pairs."""
+    R = scene.kernel_radius * scene.h
+    p_out = oracle.params(scene, kernel_radius=(R + band * scene.h) / scene.h)
+    off, idx = oracle.neighbors(p_out, scene.pos)
+    pos = scene.pos
+    size = np.array(scene.size)
+    fluid = scene.ptype == 0
+    total = 0
+    for i in sample:
+        js = idx[off[i]:off[i + 1]]
+        d = pos[i][None, :] - pos[js]
+        for a in range(3):
+            if (scene.periodic >> a) & 1:
+                d[:, a] -= size[a] * np.round(d[:, a] / size[a])
+        r = np.sqrt((d * d).sum(1))
+        sure = js[r < R - band * scene.h]
+        near = set(js[np.abs(r - R) <= band * scene.h].tolist())
+        if not fluid[i]:
+            sure = sure[fluid[sure]]
+        nf, nb = int(counts[i, 0]), int(counts[i, 1])
+        got = ids[i, :nf + nb]
+        assert len(set(got.tolist())) == nf + nb, f"duplicate neighbours of {i}"
+        assert np.all(fluid[got[:nf]]) and not np.any(fluid[got[nf:nf + nb]]), f"list parts of {i}"
+        g = set(got.tolist()) - near
+        assert g == set(sure.tolist()), f"particle {i}: gpu-oracle {sorted(g - set(sure.tolist()))} " \
+                                        f"oracle-gpu {sorted(set(sure.tolist()) - g)}"
+        total += len(sure)
+    return total

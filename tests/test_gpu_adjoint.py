@@ -135,3 +135,42 @@ def test_adjoint_32cube_T64_64_directions():
     for k, v in enumerate(fd_dirs):
         gv = float(np.sum(g * v.reshape(-1, 3)))
         assert abs(gv - fd[k]) <= TOL * max(abs(fd[k]), np.sqrt(np.mean(J ** 2))), (gv, fd[k])
+
+
+def test_rollout_refuses_a_replaced_recording():
+    # two rollouts on one context: the second forward replaces the first's tape, so the
+    # first's backward must refuse instead of returning the second trajectory's gradients;
+    # the second's own backward still works and matches a fresh context's gradient
+    import torch
+    from paper_2207_11328_gb300.autograd import rollout
+    s, tgt = _box(8)
+    dev = torch.device("cuda", 0)
+    sim = sim_for(s)
+    args = (sim, torch.tensor(s.pos, device=dev), torch.tensor(s.delta), torch.tensor(s.mass), torch.tensor(s.ptype))
+    u_a = torch.tensor(s.vel, dtype=torch.float32, device=dev, requires_grad=True)
+    u_b = torch.tensor(s.vel, dtype=torch.float32, device=dev, requires_grad=True)
+    al = torch.tensor(s.alpha, dtype=torch.float64, requires_grad=True)
+    g0 = sim.tape_generation()
+    x_a = rollout(u_a, al, *args, T=4, K=2)
+    g1 = sim.tape_generation()
+    x_b = rollout(u_b, al, *args, T=4, K=2)
+    g2 = sim.tape_generation()
+    assert g1 > g0 and g2 > g1
+    with pytest.raises(RuntimeError, match="replaced"):
+        x_a.sum().backward()
+    x_b.sum().backward()
+    _, g_ref, _, _ = _gpu_grad_sum(s, T=4, K=2)
+    assert np.array_equal(u_b.grad.cpu().numpy(), g_ref)
+
+
+def _gpu_grad_sum(s, T, K):
+    import torch
+    from paper_2207_11328_gb300.autograd import rollout
+    dev = torch.device("cuda", 0)
+    sim = sim_for(s)
+    u0 = torch.tensor(s.vel, dtype=torch.float32, device=dev, requires_grad=True)
+    al = torch.tensor(s.alpha, dtype=torch.float64, requires_grad=True)
+    x = rollout(u0, al, sim, torch.tensor(s.pos, device=dev), torch.tensor(s.delta), torch.tensor(s.mass),
+                torch.tensor(s.ptype), T=T, K=K)
+    x.sum().backward()
+    return None, u0.grad.cpu().numpy(), float(al.grad), sim

@@ -110,23 +110,56 @@ def test_poiseuille_series_itself():
     assert np.allclose(poiseuille_profile(y, 50.0), 0.01 * (0.25 - y * y) / 0.2, rtol=1e-9)
 
 
-def test_poiseuille_converges_to_closed_form():
-    # laminar channel at t = 1 s: L2 error vs the closed form <= 3.5% of u_max
-    # at 32 particles across and falling at first order in dp (16 -> 32)
-    errs = []
+@pytest.fixture(scope="module")
+def channel_runs():
+    # the plane channel at 16 and 32 particles across (nx = nz = 8), stepped by the
+    # oracle from rest to t = 5 s; the states at t = 1 s and t = 5 s are kept
+    out = {}
     for ny in (16, 32):
         s = scenes.poiseuille(dp=1.0 / ny, nx=8, ny=ny, nz=8)
         p = oracle.params(s)
         x, u, d, dt, t = s.pos, s.vel.astype(float), s.delta.astype(float), 0.0, 0.0
-        while t < 1.0 - 1e-12:
-            x, u, d, dt, dts = oracle.step(p, x, u, d, s.mass, s.ptype, 1, dt)
-            t += dts[0]
+        for t_end in (1.0, 5.0):
+            while t < t_end - 1e-12:
+                x, u, d, dt, dts = oracle.step(p, x, u, d, s.mass, s.ptype, 1, dt)
+                t += dts[0]
+            out[(ny, t_end)] = (s, x.copy(), u.copy(), t)
+    return out
+
+
+def test_poiseuille_converges_to_closed_form(channel_runs):
+    # laminar channel at t = 1 s: L2 error vs the closed form <= 3.5% of u_max
+    # at 32 particles across and falling at first order in dp (16 -> 32)
+    errs = []
+    for ny in (16, 32):
+        s, x, u, t = channel_runs[(ny, 1.0)]
         f = s.ptype == 0
         ref = poiseuille_profile(x[f, 1], t)
         errs.append(np.sqrt(np.mean((u[f, 0] - ref) ** 2)) / 0.0125)
         assert np.max(np.abs(u[f, 1:])) < 1e-3 * 0.0125   # no cross-flow
     assert errs[1] < 0.035
     assert 1.5 < errs[0] / errs[1] < 2.5
+
+
+def test_poiseuille_steady_state(channel_runs):
+    # the same channel at t = 5 s (five time constants 4a^2/(pi^2 nu)): the profile has
+    # reached the parabola u = F (a^2 - y^2)/(2 nu).  Dynamic boundary particles hold
+    # u = 0 at their own positions, so the no-slip plane is the first boundary layer
+    # y = +-(a + dp/2): against it the L2 error is <= 2.5% of u_max at 16 and 32 across;
+    # against the plates at +-a the error is the O(dp) offset of that plane, falling at
+    # first order (16 -> 32).
+    errs_a, errs_w = [], []
+    for ny in (16, 32):
+        s, x, u, t = channel_runs[(ny, 5.0)]
+        f = s.ptype == 0
+        for errs, aw in ((errs_a, 0.5), (errs_w, 0.5 + 0.5 / ny)):
+            ref = poiseuille_profile(x[f, 1], t, a=aw)
+            errs.append(np.sqrt(np.mean((u[f, 0] - ref) ** 2)) / (0.01 * aw * aw / 0.2))
+        # the series at t = 5 s is the parabola to 0.8% of u_max
+        assert np.max(np.abs(poiseuille_profile(x[f, 1], t) - 0.01 * (0.25 - x[f, 1] ** 2) / 0.2)) < 0.008 * 0.0125
+        assert np.max(np.abs(u[f, 1:])) < 2e-3 * 0.0125   # no cross-flow
+    assert max(errs_w) <= 0.025
+    assert 1.5 < errs_a[0] / errs_a[1] < 2.5
 
 
 @pytest.fixture(scope="module")

@@ -67,6 +67,8 @@ MUTANTS = [
      "delta[i] = delta[i] + T(dt) * drho[i];"),
     ("CFL acceleration branch", "dt = std::min(dt, std::sqrt(P.h / std::sqrt(amax2)));",
      "dt = std::min(dt, P.h / std::sqrt(amax2));"),
+    ("viscous time step scaled by the CFL factor", "dt = std::min(dt, kViscousDtCoef * P.h * P.h / P.nu);",
+     "dt = std::min(dt, P.cfl * P.h * P.h / P.nu);"),
     ("dual sqrt derivative", "return Dual(s, a.d / (2.0 * s));", "return Dual(s, a.d / s);"),
     ("dual product rule", "return Dual(a.v * b.v, a.d * b.v + a.v * b.d);", "return Dual(a.v * b.v, a.d * b.v);"),
 ]
@@ -84,7 +86,7 @@ BATTERY = [
     lambda: tn.test_brute_matches_numpy(7), lambda: tn.test_grid_matches_brute(7), tn.test_lattice_interior_count_is_80,
     tp.test_continuity_linear_field, tp.test_continuity_sign_approaching_pair, tp.test_pressure_gradient_linear_density,
     tp.test_mass_factor_in_pressure_term, tp.test_artificial_viscosity_switch, tp.test_laminar_shear_closed_form,
-    tp.test_boundary_particles, tp.test_cfl_dt_branches,
+    tp.test_boundary_particles, tp.test_cfl_dt_branches, tp.test_viscous_time_step_is_within_the_stable_range,
     lambda: tp.test_momentum_conserved_periodic(1, 0.0, 0.1),
     lambda: ti.test_jvp_matches_central_differences_smooth(_box8()),
     ti.test_first_dt_from_initial_forces_and_cfl,

@@ -174,7 +174,7 @@ def test_boundary_particles():
 
 
 def test_cfl_dt_branches():
-    # C7: dt = cfl * min(sqrt(h/|a|max), h/c0, h^2/nu)
+    # C7: dt = min(cfl * min(sqrt(h/|a|max), h/c0), 0.125 h^2/nu)
     p = _params(cfl=0.3, c0=20.0)
     h = 1.3 * DP
     a = np.array([[0, 0, 0.0], [3.0, 4.0, 0.0]])
@@ -185,7 +185,37 @@ def test_cfl_dt_branches():
     # boundary accelerations are ignored
     assert oracle.cfl_dt(p, a_big, np.ones(1, np.uint8)) == pytest.approx(0.3 * h / 20.0)
     pl = _params(cfl=0.3, c0=1.0, visc_model=1, nu=0.1)
-    assert oracle.cfl_dt(pl, np.zeros((1, 3)), np.zeros(1, np.uint8)) == pytest.approx(0.3 * h * h / 0.1)
+    assert oracle.cfl_dt(pl, np.zeros((1, 3)), np.zeros(1, np.uint8)) == pytest.approx(0.125 * h * h / 0.1)
+    # the viscous limit does not scale with the CFL factor
+    pl2 = _params(cfl=0.6, c0=1.0, visc_model=1, nu=0.1)
+    assert oracle.cfl_dt(pl2, np.zeros((1, 3)), np.zeros(1, np.uint8)) == pytest.approx(0.125 * h * h / 0.1)
+
+
+def test_viscous_time_step_is_within_the_stable_range():
+    # The laminar (Morris) term's fastest mode on the lattice: u_x = eps (-1)^(i+j+k),
+    # neighbours of odd parity move against the particle.  Its decay rate lambda = -a_x/u_x
+    # comes from the oracle's own right-hand side.  The two-stage predictor-corrector
+    # u* = u + dt/2 a(u), u' = u + dt a(u*) multiplies this mode by 1 - z + z^2/2 with
+    # z = lambda dt, which stays within [-1, 1] only for 0 <= z <= 2.  The viscous
+    # limit of the time step must keep z <= 2; the CFL factor 0.3 applied to h^2/nu
+    # would not (it is the limit that made a 64-across channel blow up after ~2 s).
+    n, nu = 12, 0.1
+    s = scenes.periodic_box(n_per_axis=n, dp=DP)
+    p = oracle.params(s, visc_model=1, nu=nu, alpha=0.0, c0=1.0, g=(0.0, 0.0, 0.0))
+    ijk = np.round(s.pos / DP - 0.5).astype(int)
+    sign = (-1.0) ** ijk.sum(1)
+    vel = np.zeros((s.n, 3))
+    vel[:, 0] = 1e-3 * sign
+    a, _ = oracle.rhs(p, s.pos, vel, np.zeros(s.n), s.mass, s.ptype)
+    lam = -a[:, 0] / vel[:, 0]
+    assert np.allclose(lam, lam[0], rtol=1e-9) and lam[0] > 0      # an eigenmode of the lattice
+    h = s.h
+    assert 6.0 * nu / h ** 2 < lam[0] < 8.0 * nu / h ** 2            # ~ 4 nu sum_odd |F| dp^3 = 7 nu/h^2
+    dt = oracle.cfl_dt(p, np.zeros((s.n, 3)), s.ptype)
+    z = lam[0] * dt
+    assert dt == pytest.approx(0.125 * h * h / nu) and abs(1 - z + z * z / 2) <= 1.0
+    z_old = lam[0] * 0.3 * h * h / nu
+    assert abs(1 - z_old + z_old * z_old / 2) > 1.0
 
 
 def test_artificial_viscosity_shear_decay():

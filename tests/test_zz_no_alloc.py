@@ -25,23 +25,28 @@ def _call_noalloc(sim):
     return counts, ids
 
 
-def test_noalloc_download_matches_allocating_download():
-    require_gpu()
-    s = scenes.periodic_box(n_per_axis=16, jitter=0.3, seed=21)
-    sim = sim_for(s)
+def _check_twice(sim):
     ref_counts, ref_ids = sim.download_neighbors()
     for _ in range(2):
         counts, ids = _call_noalloc(sim)
         assert np.array_equal(counts, ref_counts)
         assert np.array_equal(ids, ref_ids)
-    # a different, smaller state next: stale entries of the previous call must not show
-    d = scenes.dam_break(dp=0.04)
-    sim2 = sim_for(d)
-    ref_counts, ref_ids = sim2.download_neighbors()
-    for _ in range(2):
-        counts, ids = _call_noalloc(sim2)
-        assert np.array_equal(counts, ref_counts)
-        assert np.array_equal(ids, ref_ids)
+
+
+def test_noalloc_download_matches_allocating_download():
+    require_gpu()
+    # the larger state first (10,204 particles), then a smaller one (4,096): the second
+    # state's slots of the shared array still hold the first state's ids, so a call that
+    # failed to reset them would return stale ids in the unused (0xFFFFFFFF) slots
+    big = scenes.dam_break(dp=0.04)
+    small = scenes.periodic_box(n_per_axis=16, jitter=0.3, seed=21)
+    assert big.n > small.n
+    sim_big = sim_for(big)
+    _check_twice(sim_big)
+    sim_small = sim_for(small)
+    _check_twice(sim_small)
+    # and back to the larger one: nothing of the smaller call leaks into it either
+    _check_twice(sim_big)
 
 
 def test_noalloc_download_rejects_oversize():
