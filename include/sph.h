@@ -239,8 +239,10 @@ int sph_set_alpha(sph_ctx* ctx, double alpha);
  * uploaded state with dt frozen at params.dt_fixed, or (if that is <= 0) at
  * the CFL dt of one forces call on the initial state (*dt_out, nullable),
  * storing a checkpoint of the state every K steps (T % K == 0).  One scene
- * only.  Allocates its checkpoints and tape (about 48 B per particle per
- * checkpoint, ~180 B per particle per step of one segment).  Afterwards
+ * only.  Allocates its checkpoints and tape: 48 B per particle per
+ * checkpoint, and per step of one segment 80 B per particle of states plus
+ * a neighbour-list slot (8 * (max_neibs/2 + 1) + 4 B per particle), where
+ * sph_backward keeps each recomputed step's list for its reversal.  Afterwards
  * the context holds the state after T steps.  Synchronises `stream`. */
 int sph_record(sph_ctx* ctx, uint32_t T, uint32_t K, void* stream, double* dt_out);
 

@@ -38,47 +38,6 @@ __device__ __forceinline__ float eos_dphat(float d, const Phys& ph, float phat_c
     return phat_coef * (g * pw * inv * inv * inv - 2.0f * (pw - 1.0f) * inv * inv * inv);
 }
 
-__global__ void k_adj_dphat(const float4* __restrict__ vel, const float4* __restrict__ vel_s,
-                            const uint32_t* __restrict__ pinfo, const SceneDev* __restrict__ scenes,
-                            const DevStatus* __restrict__ st, float* __restrict__ dphat, float* __restrict__ dphat_s,
-                            const Phys ph) {
-    const uint32_t n = st->n_active;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const float c = scenes[pinfo[i]].phat_coef;
-        dphat[i] = eos_dphat(vel[i].w, ph, c);
-        dphat_s[i] = eos_dphat(vel_s[i].w, ph, c);
-    }
-}
-
-// id space <-> sorted order of the step
-__global__ void k_adj_gather(const uint32_t* __restrict__ pid, const DevStatus* __restrict__ st,
-                             const float4* __restrict__ xb_id, const float4* __restrict__ ub_id,
-                             float4* __restrict__ xb, float4* __restrict__ ub) {
-    const uint32_t n = st->n_active;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t id = pid[i];
-        xb[i] = xb_id[id];
-        ub[i] = ub_id[id];
-    }
-}
-
-// (x, u of boundary particles are constants: their adjoints are dropped here)
-__global__ void k_adj_scatter(const uint32_t* __restrict__ pid, const float4* __restrict__ pos,
-                              const DevStatus* __restrict__ st, const float4* __restrict__ xb,
-                              const float4* __restrict__ ub, float4* __restrict__ xb_id, float4* __restrict__ ub_id) {
-    const uint32_t n = st->n_active;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t id = pid[i];
-        float4 x = xb[i], u = ub[i];
-        if (!(pos[i].w > 0.f)) {
-            x.x = x.y = x.z = 0.f;
-            u.x = u.y = u.z = 0.f;
-        }
-        xb_id[id] = x;
-        ub_id[id] = u;
-    }
-}
-
 // user layout (n*3, n floats; NULL = zero) <-> id-space float4 adjoints
 __global__ void k_adj_load(uint32_t n, const float* __restrict__ xbar, const float* __restrict__ ubar,
                            const float* __restrict__ dbar, float4* __restrict__ xb_id, float4* __restrict__ ub_id) {
@@ -109,19 +68,31 @@ __global__ void k_adj_store(uint32_t n, const float4* __restrict__ xb_id, const 
     }
 }
 
-// reverse of the corrector: adjoint of state n+1 (in xb, ub) -> seeds at *
-// and the partial adjoint of state n (in place)
-__global__ void k_adj_corrector(const float4* __restrict__ pos, const DevStatus* __restrict__ st, float dt,
-                                float inv_rho0, float4* __restrict__ xb, float4* __restrict__ ub,
-                                float4* __restrict__ seed) {
+// Start of one reversed step, per particle (sorted order of the step):
+//   d(P/rho^2)/d delta at n and at *; the adjoint of state n+1 gathered from id
+//   space; reverse of the corrector: the seeds of the VJP at * and the partial
+//   adjoint of state n.
+//   x' = x + dt/2 (u + u'), u' = u + dt a*, delta' = delta + dt drho*/rho0:
+//   u'bar_tot = u'bar + dt/2 x'bar;  ubar_n = u'bar_tot + dt/2 x'bar;
+//   seeds at *: abar = dt u'bar_tot, drhobar = dt/rho0 delta'bar.
+__global__ void k_adj_pre(const float4* __restrict__ pos, const float4* __restrict__ vel,
+                          const float4* __restrict__ vel_s, const uint32_t* __restrict__ pinfo,
+                          const uint32_t* __restrict__ pid, const SceneDev* __restrict__ scenes,
+                          const DevStatus* __restrict__ st, const Phys ph, float dt,
+                          const float4* __restrict__ xb_id, const float4* __restrict__ ub_id,
+                          float* __restrict__ dphat, float* __restrict__ dphat_s, float4* __restrict__ xb,
+                          float4* __restrict__ ub, float4* __restrict__ seed) {
     const uint32_t n = st->n_active;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const float c = scenes[pinfo[i]].phat_coef;
+        dphat[i] = eos_dphat(vel[i].w, ph, c);
+        dphat_s[i] = eos_dphat(vel_s[i].w, ph, c);
+        const uint32_t id = pid[i];
         const bool fluid = pos[i].w > 0.f;
-        float4 x = xb[i], u = ub[i];
+        float4 x = xb_id[id], u = ub_id[id];
         const float dbar = x.w;
-        float4 sd = make_float4(0.f, 0.f, 0.f, dt * inv_rho0 * dbar);
+        float4 sd = make_float4(0.f, 0.f, 0.f, dt * ph.inv_rho0 * dbar);
         if (fluid) {
-            // x' = x + dt/2 (u + u'):  u'bar_tot = u'bar + dt/2 x'bar;  ubar_n = u'bar_tot + dt/2 x'bar
             const float hx = 0.5f * dt * x.x, hy = 0.5f * dt * x.y, hz = 0.5f * dt * x.z;
             const float tx = u.x + hx, ty = u.y + hy, tz = u.z + hz;
             sd.x = dt * tx;
@@ -140,71 +111,69 @@ __global__ void k_adj_corrector(const float4* __restrict__ pos, const DevStatus*
     }
 }
 
-// reverse of the predictor: star adjoint (xbs, ubs) -> partial adjoint of n
-// (+=) and seeds at n
-__global__ void k_adj_predictor(const float4* __restrict__ pos, const DevStatus* __restrict__ st, float dt,
-                                float inv_rho0, const float4* __restrict__ xbs, const float4* __restrict__ ubs,
-                                float4* __restrict__ xb, float4* __restrict__ ub, float4* __restrict__ seed) {
-    const uint32_t n = st->n_active;
+// Tape copies: n elements of each of `count` arrays (16- or 4-byte elements)
+// between the particle buffers and a flat tape block, one launch per copy.
+struct TapeCopy {
+    const void* src[kTapeArrays];
+    void* dst[kTapeArrays];
+    uint32_t wide;  // bit k: array k has 16-byte elements
+    int count;
+};
+
+__global__ void k_tape_copy(const TapeCopy tc, uint32_t n) {
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const bool fluid = pos[i].w > 0.f;
-        const float h = 0.5f * dt;
-        const float4 xs = xbs[i], us = ubs[i];
-        float4 x = xb[i], u = ub[i];
-        float4 sd = make_float4(0.f, 0.f, 0.f, h * inv_rho0 * xs.w);
-        x.w += xs.w;
-        u.w += us.w;  // alphabar partial of the star VJP
-        if (fluid) {
-            x.x += xs.x;
-            x.y += xs.y;
-            x.z += xs.z;
-            u.x += h * xs.x + us.x;
-            u.y += h * xs.y + us.y;
-            u.z += h * xs.z + us.z;
-            sd.x = h * us.x;
-            sd.y = h * us.y;
-            sd.z = h * us.z;
+#pragma unroll
+        for (int k = 0; k < kTapeArrays; ++k) {
+            if (k >= tc.count) break;
+            if ((tc.wide >> k) & 1u)
+                static_cast<float4*>(tc.dst[k])[i] = static_cast<const float4*>(tc.src[k])[i];
+            else
+                static_cast<uint32_t*>(tc.dst[k])[i] = static_cast<const uint32_t*>(tc.src[k])[i];
         }
-        xb[i] = x;
-        ub[i] = u;
-        seed[i] = sd;
     }
 }
 
-struct PairIn {
-    float rx, ry, rz, r2;   // x_ij
-    float ux, uy, uz;       // u_ij
-    float di, dj;           // delta_i, delta_j
-    float phi, phj;         // P/rho^2
-    float dphi, dphj;       // d(P/rho^2)/d delta
-    float m;                // m_j
-    float Ax, Ay, Az, rb;   // adjoint seeds of particle i's a and drho
+// Both terms of pair (k, j) that the VJP of particle k needs, evaluated together:
+// its own term T_kj seeded with k's adjoints (abar_k, drhobar_k) and the
+// neighbour's term T_jk seeded with j's.  Everything that depends on the pair
+// alone (r, F, F'/r, u.x, the viscosity switch and its derivatives) is
+// symmetric and computed once: x_jk = -x_kj and u_jk = -u_kj leave u.x, r and
+// Pi unchanged and flip the odd derivatives.  Returns the derivative of
+// S_kj + S_jk w.r.t. x_k, u_k and delta_k, and of S_kj w.r.t. alpha (T_jk's
+// alpha derivative belongs to particle j).  Same sums as two calls of
+// pair_grad (own term plus the neighbour's term, transposed).
+struct PairIn2 {
+    float rx, ry, rz, r2;   // x_kj
+    float ux, uy, uz;       // u_kj
+    float dk, dj;           // delta_k, delta_j
+    float phk, phj, dphk;   // P/rho^2 of k and j, d(P/rho^2)/d delta of k
+    float mj, mk;
+    float3 Ak, Aj;          // abar of k and j
+    float rbk, rbj;         // drhobar of k and j
 };
 
-struct PairGrad {
-    float gx, gy, gz;       // d S / d x_ij
-    float gux, guy, guz;    // d S / d u_ij
-    float gdi, gdj, ga;     // d S / d delta_i, d delta_j, d alpha
+struct PairGrad2 {
+    float gx, gy, gz, gux, guy, guz, gd, ga;
 };
 
-// S = A . a_ij + rb * drho_ij for one pair term of particle i (see forces.cu).
 template <int VISC>
-__device__ __forceinline__ PairGrad pair_grad(const PairIn& p, const Phys& ph, float pic, float pic_unit) {
-    PairGrad g;
+__device__ __forceinline__ PairGrad2 pair_grad2(const PairIn2& p, const Phys& ph, float pic, float pic_unit) {
+    PairGrad2 g;
     const float r2 = fmaxf(p.r2, 1e-30f);
     const float r = r2 * rsqrtf(r2);
     const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
     const float F = ph.aF * t * t * t;
     const float Fr = 3.0f * ph.aF * t * t * ph.inv_h / r;  // (dF/dr)/r
     const float w = fmaf(p.ux, p.rx, fmaf(p.uy, p.ry, p.uz * p.rz));
-    const float s = fmaf(p.Ax, p.rx, fmaf(p.Ay, p.ry, p.Az * p.rz));
+    const float sa = fmaf(p.Ak.x, p.rx, fmaf(p.Ak.y, p.ry, p.Ak.z * p.rz));      // abar_k . x_kj
+    const float sb = -fmaf(p.Aj.x, p.rx, fmaf(p.Aj.y, p.ry, p.Aj.z * p.rz));     // abar_j . x_jk
     float Pi = 0.f, dPx = 0.f, dPy = 0.f, dPz = 0.f, dPux = 0.f, dPuy = 0.f, dPuz = 0.f, dPd = 0.f, dPa = 0.f;
     if (VISC == SPH_VISC_ARTIFICIAL && w < 0.f) {
-        const float E = fmaf(0.5f, p.di + p.dj, 1.0f);
+        const float E = fmaf(0.5f, p.dk + p.dj, 1.0f);
         const float D = r2 + ph.eps_h2;
         const float inv = 1.0f / (D * E);
         Pi = -pic * w * inv;
-        const float k = -pic * inv;             // dPi/du = k x ; dPi/dx = k (u - 2 w x / D)
+        const float k = -pic * inv;             // dPi/du_kj = k x ; dPi/dx_kj = k (u - 2 w x / D)
         const float c2 = 2.0f * w / D;
         dPx = k * (p.ux - c2 * p.rx);
         dPy = k * (p.uy - c2 * p.ry);
@@ -212,52 +181,71 @@ __device__ __forceinline__ PairGrad pair_grad(const PairIn& p, const Phys& ph, f
         dPux = k * p.rx;
         dPuy = k * p.ry;
         dPuz = k * p.rz;
-        dPd = -0.5f * Pi / E;                    // dPi/d delta_i = dPi/d delta_j
+        dPd = -0.5f * Pi / E;                    // dPi/d delta_k = dPi/d delta_j
         dPa = -pic_unit * w * inv;               // dPi/d alpha
     }
-    const float Bc = -p.m * (p.phi + p.phj + Pi);
-    const float mF = p.m * F;
-    const float cFr = (s * Bc + p.rb * p.m * w) * Fr;
-    const float sFm = -s * mF;                   // s F (-m)
-    g.gx = Bc * F * p.Ax + cFr * p.rx + p.rb * mF * p.ux + sFm * dPx;
-    g.gy = Bc * F * p.Ay + cFr * p.ry + p.rb * mF * p.uy + sFm * dPy;
-    g.gz = Bc * F * p.Az + cFr * p.rz + p.rb * mF * p.uz + sFm * dPz;
-    g.gux = sFm * dPux + p.rb * mF * p.rx;
-    g.guy = sFm * dPuy + p.rb * mF * p.ry;
-    g.guz = sFm * dPuz + p.rb * mF * p.rz;
-    g.gdi = sFm * (p.dphi + dPd);
-    g.gdj = sFm * (p.dphj + dPd);
-    g.ga = sFm * dPa;
+    const float S = p.phk + p.phj + Pi;
+    const float Bca = -p.mj * S, Bcb = -p.mk * S;
+    const float mFa = p.mj * F, mFb = p.mk * F;
+    const float sFma = -sa * mFa, sFmb = -sb * mFb;
+    const float C1 = (sa * Bca + p.rbk * p.mj * w) * Fr + (sb * Bcb + p.rbj * p.mk * w) * Fr;
+    const float C2 = p.rbk * mFa + p.rbj * mFb;
+    const float C3 = sFma + sFmb;
+    g.gx = F * (Bca * p.Ak.x - Bcb * p.Aj.x) + C1 * p.rx + C2 * p.ux + C3 * dPx;
+    g.gy = F * (Bca * p.Ak.y - Bcb * p.Aj.y) + C1 * p.ry + C2 * p.uy + C3 * dPy;
+    g.gz = F * (Bca * p.Ak.z - Bcb * p.Aj.z) + C1 * p.rz + C2 * p.uz + C3 * dPz;
+    g.gux = C3 * dPux + C2 * p.rx;
+    g.guy = C3 * dPuy + C2 * p.ry;
+    g.guz = C3 * dPuz + C2 * p.rz;
+    g.gd = C3 * (p.dphk + dPd);
+    g.ga = sFma * dPa;
     if (VISC == SPH_VISC_LAMINAR) {
-        // a_ij += lam m F u / (2 + di + dj), lam = 4 nu / rho0
-        const float inv2 = 1.0f / (2.0f + p.di + p.dj);
+        // a_kj += lam m_j F u_kj / (2 + d_k + d_j), lam = 4 nu / rho0 (and a_jk likewise with m_k)
+        const float inv2 = 1.0f / (2.0f + p.dk + p.dj);
         const float lam = ph.nu4 * ph.inv_rho0 * inv2;
-        const float Au = fmaf(p.Ax, p.ux, fmaf(p.Ay, p.uy, p.Az * p.uz));
-        const float cx = lam * p.m * Au * Fr;
+        const float Aua = fmaf(p.Ak.x, p.ux, fmaf(p.Ak.y, p.uy, p.Ak.z * p.uz));
+        const float Aub = -fmaf(p.Aj.x, p.ux, fmaf(p.Aj.y, p.uy, p.Aj.z * p.uz));
+        const float cx = lam * (p.mj * Aua + p.mk * Aub) * Fr;
         g.gx += cx * p.rx;
         g.gy += cx * p.ry;
         g.gz += cx * p.rz;
-        g.gux += lam * mF * p.Ax;
-        g.guy += lam * mF * p.Ay;
-        g.guz += lam * mF * p.Az;
-        const float dd = -lam * mF * Au * inv2;
-        g.gdi += dd;
-        g.gdj += dd;
+        g.gux += lam * (mFa * p.Ak.x - mFb * p.Aj.x);
+        g.guy += lam * (mFa * p.Ak.y - mFb * p.Aj.y);
+        g.guz += lam * (mFa * p.Ak.z - mFb * p.Aj.z);
+        g.gd += -lam * inv2 * (mFa * Aua + mFb * Aub);
     }
     return g;
 }
 
 // VJP of f on one state: for every particle k, the derivative of
-// sum_i (abar_i . a_i + drhobar_i drho_i) w.r.t. x_k, u_k, delta_k, alpha.
-// ACCUM: add to (xb, ub) instead of assigning.
-template <int VISC, bool ACCUM>
+// sum_i (abar_i . a_i + drhobar_i drho_i) w.r.t. x_k, u_k, delta_k, alpha,
+// followed by the particle's next reverse stage (no separate launch):
+//   STAR (the VJP at the predicted state): reverse of the predictor,
+//     x* = x + h u, u* = u + h a, delta* = delta + h drho/rho0 (h = dt/2):
+//     xbar_n += x*bar, ubar_n += h x*bar + u*bar, deltabar_n += delta*bar,
+//     seeds at n: abar = h u*bar, drhobar = h/rho0 delta*bar  -> (xb, ub, seed_n);
+//   otherwise (the VJP at n): adds to (xb, ub) and writes the step's result to
+//     id space (x and u of boundary particles are constants: dropped).
+// LANES consecutive lanes share one particle: lane l of the group takes the list
+// entries q = l (mod LANES), and the partial sums are combined by a fixed xor
+// tree of shuffles, so the result is deterministic (for a given LANES).  More
+// lanes per particle keep small states (the differentiable run's 32^3 box) from
+// leaving most of the GPU idle.
+template <int VISC, bool STAR, int LANES>
 __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     const float* __restrict__ dphat, const float4* __restrict__ seed, const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount, const SceneDev* __restrict__ scenes,
-    const DevStatus* __restrict__ st, const Phys ph, float4* __restrict__ xb, float4* __restrict__ ub) {
+    const DevStatus* __restrict__ st, const Phys ph, float dt, const uint32_t* __restrict__ pid,
+    float4* __restrict__ xb, float4* __restrict__ ub, float4* __restrict__ seed_n, float4* __restrict__ xb_id,
+    float4* __restrict__ ub_id) {
+    static_assert(LANES == 1 || LANES == 2 || LANES == 4 || LANES == 8, "a power of two within a warp");
     const uint32_t n = st->n_active;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t sub = tid % LANES;
+    const unsigned gmask = LANES == 1 ? 0xffffffffu
+                                      : ((1u << LANES) - 1u) << ((threadIdx.x & 31u) & ~(uint32_t)(LANES - 1));
+    for (uint32_t k = tid / LANES; k < n; k += (gridDim.x * blockDim.x) / LANES) {
         const SceneDev& sc = scenes[pinfo[k]];
         const float4 pk = pos[k];
         const float4 vk = vel[k];
@@ -267,7 +255,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
         const uint32_t cnt = ncount[k];
         const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
         float gx = 0.f, gy = 0.f, gz = 0.f, gux = 0.f, guy = 0.f, guz = 0.f, gd = 0.f, ga = 0.f;
-        for (uint32_t q = 0; q < nf + nb; ++q) {
+        for (uint32_t q = sub; q < nf + nb; q += LANES) {
             const uint32_t e = nlist[q < nf ? list_fluid_word(q, k, ph.stride)
                                             : list_bnd_word(q - nf, k, ph.stride, ph.max_neibs)];
             const uint32_t j = e >> kCodeBits;
@@ -275,7 +263,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
             const float4 pj = pos[j];
             const float4 vj = vel[j];
             const float4 sj = seed[j];
-            PairIn in;
+            PairIn2 in;
             in.rx = pk.x - pj.x - cell_delta(e & 3u, sc.cell_f[0]);
             in.ry = pk.y - pj.y - cell_delta((e >> 2) & 3u, sc.cell_f[1]);
             in.rz = pk.z - pj.z - cell_delta((e >> 4) & 3u, sc.cell_f[2]);
@@ -283,67 +271,89 @@ __global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
             in.ux = vk.x - vj.x;
             in.uy = vk.y - vj.y;
             in.uz = vk.z - vj.z;
-            // own term T_kj, seeded with k's adjoints
-            in.di = vk.w;
+            in.dk = vk.w;
             in.dj = vj.w;
-            in.phi = phk;
+            in.phk = phk;
             in.phj = phat[j];
-            in.dphi = dphk;
-            in.dphj = dphat[j];
-            in.m = fabsf(pj.w);
-            in.Ax = sk.x;
-            in.Ay = sk.y;
-            in.Az = sk.z;
-            in.rb = sk.w;
-            const PairGrad a = pair_grad<VISC>(in, ph, sc.pi_coef, sc.pi_unit);
-            gx += a.gx;
-            gy += a.gy;
-            gz += a.gz;
-            gux += a.gux;
-            guy += a.guy;
-            guz += a.guz;
-            gd += a.gdi;
-            ga += a.ga;
-            // neighbour's term T_jk (x_jk = -x_kj, u_jk = -u_kj), seeded with j's adjoints
-            PairIn rv = in;
-            rv.rx = -in.rx;
-            rv.ry = -in.ry;
-            rv.rz = -in.rz;
-            rv.ux = -in.ux;
-            rv.uy = -in.uy;
-            rv.uz = -in.uz;
-            rv.di = in.dj;
-            rv.dj = in.di;
-            rv.phi = in.phj;
-            rv.phj = in.phi;
-            rv.dphi = in.dphj;
-            rv.dphj = in.dphi;
-            rv.m = mk;
-            rv.Ax = sj.x;
-            rv.Ay = sj.y;
-            rv.Az = sj.z;
-            rv.rb = sj.w;
-            const PairGrad b = pair_grad<VISC>(rv, ph, sc.pi_coef, sc.pi_unit);
-            gx -= b.gx;
-            gy -= b.gy;
-            gz -= b.gz;
-            gux -= b.gux;
-            guy -= b.guy;
-            guz -= b.guz;
-            gd += b.gdj;
+            in.dphk = dphk;
+            in.mj = fabsf(pj.w);
+            in.mk = mk;
+            in.Ak = make_float3(sk.x, sk.y, sk.z);
+            in.rbk = sk.w;
+            in.Aj = make_float3(sj.x, sj.y, sj.z);
+            in.rbj = sj.w;
+            const PairGrad2 g = pair_grad2<VISC>(in, ph, sc.pi_coef, sc.pi_unit);
+            gx += g.gx;
+            gy += g.gy;
+            gz += g.gz;
+            gux += g.gux;
+            guy += g.guy;
+            guz += g.guz;
+            gd += g.gd;
+            ga += g.ga;
         }
-        float4 x = ACCUM ? xb[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float4 u = ACCUM ? ub[k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        x.x += gx;
-        x.y += gy;
-        x.z += gz;
-        x.w += gd;
-        u.x += gux;
-        u.y += guy;
-        u.z += guz;
-        u.w += ga;
-        xb[k] = x;
-        ub[k] = u;
+        if (LANES > 1) {
+#pragma unroll
+            for (int o = LANES / 2; o >= 1; o >>= 1) {
+                gx += __shfl_xor_sync(gmask, gx, o);
+                gy += __shfl_xor_sync(gmask, gy, o);
+                gz += __shfl_xor_sync(gmask, gz, o);
+                gux += __shfl_xor_sync(gmask, gux, o);
+                guy += __shfl_xor_sync(gmask, guy, o);
+                guz += __shfl_xor_sync(gmask, guz, o);
+                gd += __shfl_xor_sync(gmask, gd, o);
+                ga += __shfl_xor_sync(gmask, ga, o);
+            }
+            if (sub != 0) continue;
+        }
+        const bool fluid = pk.w > 0.f;
+        if (STAR) {
+            float4 xs = make_float4(0.f, 0.f, 0.f, 0.f), us = make_float4(0.f, 0.f, 0.f, 0.f);
+            xs.x += gx;
+            xs.y += gy;
+            xs.z += gz;
+            xs.w += gd;
+            us.x += gux;
+            us.y += guy;
+            us.z += guz;
+            us.w += ga;
+            const float h = 0.5f * dt;
+            float4 x = xb[k], u = ub[k];
+            float4 sd = make_float4(0.f, 0.f, 0.f, h * ph.inv_rho0 * xs.w);
+            x.w += xs.w;
+            u.w += us.w;  // alphabar partial of the star VJP
+            if (fluid) {
+                x.x += xs.x;
+                x.y += xs.y;
+                x.z += xs.z;
+                u.x += h * xs.x + us.x;
+                u.y += h * xs.y + us.y;
+                u.z += h * xs.z + us.z;
+                sd.x = h * us.x;
+                sd.y = h * us.y;
+                sd.z = h * us.z;
+            }
+            xb[k] = x;
+            ub[k] = u;
+            seed_n[k] = sd;
+        } else {
+            float4 x = xb[k], u = ub[k];
+            x.x += gx;
+            x.y += gy;
+            x.z += gz;
+            x.w += gd;
+            u.x += gux;
+            u.y += guy;
+            u.z += guz;
+            u.w += ga;
+            if (!fluid) {
+                x.x = x.y = x.z = 0.f;
+                u.x = u.y = u.z = 0.f;
+            }
+            const uint32_t id = pid[k];
+            xb_id[id] = x;
+            ub_id[id] = u;
+        }
     }
 }
 
@@ -368,19 +378,16 @@ __global__ void k_adj_sum_alpha(const float4* __restrict__ ub_id, uint32_t n, do
 
 }  // namespace
 
-void launch_adj_dphat(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph,
+void launch_tape_copy(const void* const* src, void* const* dst, const bool* wide, int count, uint32_t n,
                       cudaStream_t st) {
-    k_adj_dphat<<<grid_for(g.cap, 256), 256, 0, st>>>(b.vel[cur], b.vel_s, b.pinfo[cur], b.scenes, b.status, a.dphat,
-                                                       a.dphat_s, ph);
-}
-
-void launch_adj_gather(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
-    k_adj_gather<<<grid_for(g.cap, 256), 256, 0, st>>>(b.pid[cur], b.status, a.xb_id, a.ub_id, a.xb, a.ub);
-}
-
-void launch_adj_scatter(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st) {
-    k_adj_scatter<<<grid_for(g.cap, 256), 256, 0, st>>>(b.pid[cur], b.pos[cur], b.status, a.xb, a.ub, a.xb_id,
-                                                         a.ub_id);
+    TapeCopy tc{};
+    tc.count = count;
+    for (int k = 0; k < count && k < kTapeArrays; ++k) {
+        tc.src[k] = src[k];
+        tc.dst[k] = dst[k];
+        tc.wide |= wide[k] ? (1u << k) : 0u;
+    }
+    k_tape_copy<<<grid_for(n ? n : 1, 256), 256, 0, st>>>(tc, n);
 }
 
 void launch_adj_load(const AdjBuffers& a, uint32_t n, const float* xbar, const float* ubar, const float* dbar,
@@ -392,30 +399,40 @@ void launch_adj_store(const AdjBuffers& a, uint32_t n, float* xbar, float* ubar,
     k_adj_store<<<grid_for(n, 256), 256, 0, st>>>(n, a.xb_id, a.ub_id, xbar, ubar, dbar);
 }
 
+template <int VISC, int LANES>
+void launch_adj_vjps(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph, float dt,
+                     cudaStream_t st) {
+    const unsigned grid = grid_for(g.cap * LANES, kBlock);
+    // VJP at the predicted state (+ reverse of the predictor), then at n (+ to id space)
+    k_adj_vjp<VISC, true, LANES><<<grid, kBlock, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, a.dphat_s, a.seed, b.pinfo[cur],
+                                                          b.nlist, b.ncount, b.scenes, b.status, ph, dt, b.pid[cur],
+                                                          a.xb, a.ub, a.seed_n, nullptr, nullptr);
+    k_adj_vjp<VISC, false, LANES><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], a.dphat, a.seed_n,
+                                                           b.pinfo[cur], b.nlist, b.ncount, b.scenes, b.status, ph,
+                                                           dt, b.pid[cur], a.xb, a.ub, nullptr, a.xb_id, a.ub_id);
+}
+
+template <int VISC>
+void launch_adj_vjps_v(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph, float dt,
+                       cudaStream_t st) {
+    // lanes per particle: enough threads to fill the GPU (~150k resident) on small states
+    if (g.cap <= (1u << 16))
+        launch_adj_vjps<VISC, 4>(a, b, cur, g, ph, dt, st);
+    else if (g.cap <= (1u << 18))
+        launch_adj_vjps<VISC, 2>(a, b, cur, g, ph, dt, st);
+    else
+        launch_adj_vjps<VISC, 1>(a, b, cur, g, ph, dt, st);
+}
+
 void launch_adj_step(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph, float dt,
                      cudaStream_t st) {
-    const unsigned grid = grid_for(g.cap, kBlock);
-    k_adj_corrector<<<grid_for(g.cap, 256), 256, 0, st>>>(b.pos[cur], b.status, dt, ph.inv_rho0, a.xb, a.ub, a.seed);
-    if (ph.visc == SPH_VISC_LAMINAR) {
-        k_adj_vjp<SPH_VISC_LAMINAR, false><<<grid, kBlock, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, a.dphat_s, a.seed,
-                                                                     b.pinfo[cur], b.nlist, b.ncount, b.scenes,
-                                                                     b.status, ph, a.xbs, a.ubs);
-    } else {
-        k_adj_vjp<SPH_VISC_ARTIFICIAL, false><<<grid, kBlock, 0, st>>>(b.pos_s, b.vel_s, b.phat_s, a.dphat_s, a.seed,
-                                                                        b.pinfo[cur], b.nlist, b.ncount, b.scenes,
-                                                                        b.status, ph, a.xbs, a.ubs);
-    }
-    k_adj_predictor<<<grid_for(g.cap, 256), 256, 0, st>>>(b.pos[cur], b.status, dt, ph.inv_rho0, a.xbs, a.ubs, a.xb,
-                                                          a.ub, a.seed);
-    if (ph.visc == SPH_VISC_LAMINAR) {
-        k_adj_vjp<SPH_VISC_LAMINAR, true><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], a.dphat, a.seed,
-                                                                    b.pinfo[cur], b.nlist, b.ncount, b.scenes,
-                                                                    b.status, ph, a.xb, a.ub);
-    } else {
-        k_adj_vjp<SPH_VISC_ARTIFICIAL, true><<<grid, kBlock, 0, st>>>(b.pos[cur], b.vel[cur], b.phat[cur], a.dphat,
-                                                                       a.seed, b.pinfo[cur], b.nlist, b.ncount,
-                                                                       b.scenes, b.status, ph, a.xb, a.ub);
-    }
+    k_adj_pre<<<grid_for(g.cap, 256), 256, 0, st>>>(b.pos[cur], b.vel[cur], b.vel_s, b.pinfo[cur], b.pid[cur], b.scenes,
+                                                    b.status, ph, dt, a.xb_id, a.ub_id, a.dphat, a.dphat_s, a.xb, a.ub,
+                                                    a.seed);
+    if (ph.visc == SPH_VISC_LAMINAR)
+        launch_adj_vjps_v<SPH_VISC_LAMINAR>(a, b, cur, g, ph, dt, st);
+    else
+        launch_adj_vjps_v<SPH_VISC_ARTIFICIAL>(a, b, cur, g, ph, dt, st);
 }
 
 void launch_adj_sum_alpha(const AdjBuffers& a, uint32_t n, double* out, cudaStream_t st) {

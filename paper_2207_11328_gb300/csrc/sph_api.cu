@@ -22,7 +22,8 @@ struct AdjTape {
     double dt = 0.0;
     Phys ph_rec{};
     std::vector<char*> ckpt;   // T/K checkpoints (pos4 vel4 phat cell pinfo pid)
-    char* steps = nullptr;     // K records (sorted state, predicted state, start, cell_nfluid)
+    char* steps = nullptr;     // K records (sorted state, predicted state)
+    char* lists = nullptr;     // K neighbour-list slots (list + counts) of the recomputed steps
     size_t ckpt_bytes = 0, step_bytes = 0;
     sphg::AdjBuffers a{};
     void* adj_mem = nullptr;
@@ -880,8 +881,10 @@ void free_tape(sph_ctx* c) {
     for (char* p : t.ckpt) cudaFree(p);
     t.ckpt.clear();
     cudaFree(t.steps);
+    cudaFree(t.lists);
     cudaFree(t.adj_mem);
     t.steps = nullptr;
+    t.lists = nullptr;
     t.adj_mem = nullptr;
     for (auto* gs : {t.seg_graph, t.rec_graph})
         for (int k = 0; k < 2; ++k)
@@ -893,79 +896,95 @@ void free_tape(sph_ctx* c) {
     t.gen = 0;
 }
 
-// copy the particle arrays of buffer `cur` to / from a flat device block
+// copy the particle arrays of buffer `cur` to / from a flat device block (one launch)
+void tape_io(const std::vector<std::pair<void*, size_t>>& arrays, char* blk, bool save, cudaStream_t st, uint32_t n) {
+    const void* src[kTapeArrays];
+    void* dst[kTapeArrays];
+    bool wide[kTapeArrays];
+    size_t off = 0;
+    int k = 0;
+    for (const auto& a : arrays) {
+        src[k] = save ? a.first : (const void*)(blk + off);
+        dst[k] = save ? (void*)(blk + off) : a.first;
+        wide[k] = a.second == sizeof(float4);
+        off += align_up(a.second * n, 256);
+        ++k;
+    }
+    launch_tape_copy(src, dst, wide, k, n, st);
+}
+
+// checkpoint: the sorted state of buffer cur (positions, velocities, P/rho^2, cell, scene, id)
 void state_io(sph_ctx* c, char* blk, bool save, cudaStream_t st, uint32_t n) {
     Buffers& b = c->b;
     const int k = c->cur;
-    size_t off = 0;
-    auto mv = [&](void* arr, size_t bytes) {
-        if (save)
-            cudaMemcpyAsync(blk + off, arr, bytes, cudaMemcpyDeviceToDevice, st);
-        else
-            cudaMemcpyAsync(arr, blk + off, bytes, cudaMemcpyDeviceToDevice, st);
-        off += align_up(bytes, 256);
-    };
-    mv(b.pos[k], sizeof(float4) * n);
-    mv(b.vel[k], sizeof(float4) * n);
-    mv(b.phat[k], sizeof(float) * n);
-    mv(b.cell[k], sizeof(uint32_t) * n);
-    mv(b.pinfo[k], sizeof(uint32_t) * n);
-    mv(b.pid[k], sizeof(uint32_t) * n);
+    tape_io({{b.pos[k], sizeof(float4)}, {b.vel[k], sizeof(float4)}, {b.phat[k], sizeof(float)},
+             {b.cell[k], sizeof(uint32_t)}, {b.pinfo[k], sizeof(uint32_t)}, {b.pid[k], sizeof(uint32_t)}},
+            blk, save, st, n);
 }
 
 size_t state_bytes(uint32_t n) {
     return 2 * align_up(sizeof(float4) * n, 256) + 4 * align_up(sizeof(uint32_t) * n, 256);
 }
 
-// sorted state + predicted state + cell tables of one step
+// one taped step: the sorted state at n and the predicted state (what the reversed step reads;
+// its neighbour list stays in the step's own list slot of the tape)
 void step_io(sph_ctx* c, char* blk, bool save, cudaStream_t st, uint32_t n) {
-    state_io(c, blk, save, st, n);
-    size_t off = state_bytes(n);
     Buffers& b = c->b;
-    auto mv = [&](void* arr, size_t bytes) {
-        if (save)
-            cudaMemcpyAsync(blk + off, arr, bytes, cudaMemcpyDeviceToDevice, st);
-        else
-            cudaMemcpyAsync(arr, blk + off, bytes, cudaMemcpyDeviceToDevice, st);
-        off += align_up(bytes, 256);
-    };
-    mv(b.pos_s, sizeof(float4) * n);
-    mv(b.vel_s, sizeof(float4) * n);
-    mv(b.phat_s, sizeof(float) * n);
-    mv(b.start, sizeof(uint32_t) * (c->g.n_cells + 2));
-    mv(b.cell_nfluid, sizeof(uint32_t) * (c->g.n_cells + 1));
+    const int k = c->cur;
+    tape_io({{b.pos[k], sizeof(float4)}, {b.vel[k], sizeof(float4)}, {b.phat[k], sizeof(float)},
+             {b.pinfo[k], sizeof(uint32_t)}, {b.pid[k], sizeof(uint32_t)}, {b.pos_s, sizeof(float4)},
+             {b.vel_s, sizeof(float4)}, {b.phat_s, sizeof(float)}},
+            blk, save, st, n);
 }
 
-size_t step_bytes(uint32_t n, uint32_t n_cells) {
-    return state_bytes(n) + 2 * align_up(sizeof(float4) * n, 256) + align_up(sizeof(float) * n, 256) +
-           align_up(sizeof(uint32_t) * (n_cells + 2), 256) + align_up(sizeof(uint32_t) * (n_cells + 1), 256);
+size_t step_bytes(uint32_t n) {
+    return 4 * align_up(sizeof(float4) * n, 256) + 4 * align_up(sizeof(uint32_t) * n, 256);
 }
 
-// one forward step with the frozen dt; optionally tape the sorted and predicted states
-void rec_step(sph_ctx* c, const Phys& ph, char* tape_blk, int advance, cudaStream_t st) {
+// neighbour-list slot of a taped step: the list (list_chunks(max_neibs) chunks of two entries
+// per particle, neighbour-major) and its counts
+size_t list_slot_bytes(const sph_ctx* c) {
+    return align_up(sizeof(uint2) * (size_t)c->ph.stride * list_chunks(c->p.max_neibs), 256) +
+           align_up(sizeof(uint32_t) * (size_t)c->g.cap, 256);
+}
+
+Buffers with_list_slot(const sph_ctx* c, char* slot) {
+    Buffers bb = c->b;
+    if (slot) {
+        bb.nlist = reinterpret_cast<uint32_t*>(slot);
+        bb.ncount = reinterpret_cast<uint32_t*>(
+            slot + align_up(sizeof(uint2) * (size_t)c->ph.stride * list_chunks(c->p.max_neibs), 256));
+    }
+    return bb;
+}
+
+// one forward step with the frozen dt; optionally tape the sorted and predicted states, and
+// build the step's list into a list slot of the tape (else into the context's list)
+void rec_step(sph_ctx* c, const Phys& ph, char* tape_blk, int advance, cudaStream_t st, char* list_slot = nullptr) {
     launch_dt(c->b, c->g, ph, advance, st);
     enqueue_sort(c, st);
-    launch_build(c->b, c->cur, c->g, ph, st);
-    launch_forces(c->b, c->cur, c->g, ph, kPredict, 0, st);
+    const Buffers bb = with_list_slot(c, list_slot);
+    launch_build(bb, c->cur, c->g, ph, st);
+    launch_forces(bb, c->cur, c->g, ph, kPredict, 0, st);
     if (tape_blk) step_io(c, tape_blk, true, st, c->tape.n);
-    launch_forces(c->b, c->cur, c->g, ph, kCorrect, 0, st);
+    launch_forces(bb, c->cur, c->g, ph, kCorrect, 0, st);
 }
 
 // one segment of the backward pass from its checkpoint (already in buffer cur):
-// recompute the K steps forward, taping every step, then reverse through them
-// (reverse corrector -> VJP at * -> reverse predictor -> VJP at n).  No host
-// synchronisation: captured once per tape and buffer parity.
+// recompute the K steps forward, taping every step's states and keeping its
+// neighbour list in the step's list slot, then reverse through them (reverse
+// corrector -> VJP at * -> reverse predictor -> VJP at n, three launches per
+// step, the list of the recomputed step reused).  No host synchronisation:
+// captured once per tape and buffer parity.
 void backward_segment(sph_ctx* c, cudaStream_t st) {
     AdjTape& t = c->tape;
     const uint32_t n = t.n;
-    for (uint32_t k = 0; k < t.K; ++k) rec_step(c, t.ph_rec, t.steps + (size_t)k * t.step_bytes, 0, st);
+    const size_t ls = list_slot_bytes(c);
+    for (uint32_t k = 0; k < t.K; ++k)
+        rec_step(c, t.ph_rec, t.steps + (size_t)k * t.step_bytes, 0, st, t.lists + (size_t)k * ls);
     for (int k = (int)t.K - 1; k >= 0; --k) {
         step_io(c, t.steps + (size_t)k * t.step_bytes, false, st, n);
-        launch_build(c->b, c->cur, c->g, t.ph_rec, st);
-        launch_adj_dphat(t.a, c->b, c->cur, c->g, t.ph_rec, st);
-        launch_adj_gather(t.a, c->b, c->cur, c->g, st);
-        launch_adj_step(t.a, c->b, c->cur, c->g, t.ph_rec, (float)t.dt, st);
-        launch_adj_scatter(t.a, c->b, c->cur, c->g, st);
+        launch_adj_step(t.a, with_list_slot(c, t.lists + (size_t)k * ls), c->cur, c->g, t.ph_rec, (float)t.dt, st);
     }
 }
 
@@ -989,7 +1008,7 @@ int alloc_tape(sph_ctx* c) {
     AdjTape& t = c->tape;
     const uint32_t n = t.n, T = t.T, K = t.K;
     t.ckpt_bytes = state_bytes(n);
-    t.step_bytes = step_bytes(n, c->g.n_cells);
+    t.step_bytes = step_bytes(n);
     for (uint32_t s2 = 0; s2 < T / K; ++s2) {
         char* p = nullptr;
         if (cudaMalloc(&p, t.ckpt_bytes) != cudaSuccess) {
@@ -1001,6 +1020,7 @@ int alloc_tape(sph_ctx* c) {
     const size_t nv = align_up(sizeof(float4) * (size_t)c->g.cap, 256);
     const size_t nf = align_up(sizeof(float) * (size_t)c->g.cap, 256);
     if (cudaMalloc((void**)&t.steps, t.step_bytes * K) != cudaSuccess ||
+        cudaMalloc((void**)&t.lists, list_slot_bytes(c) * K) != cudaSuccess ||
         cudaMalloc(&t.adj_mem, 7 * nv + 2 * nf + 256) != cudaSuccess) {
         cudaGetLastError();
         free_tape(c);
@@ -1009,9 +1029,9 @@ int alloc_tape(sph_ctx* c) {
     char* m = (char*)t.adj_mem;
     t.a.xb = (float4*)m; m += nv;
     t.a.ub = (float4*)m; m += nv;
-    t.a.xbs = (float4*)m; m += nv;
-    t.a.ubs = (float4*)m; m += nv;
     t.a.seed = (float4*)m; m += nv;
+    t.a.seed_n = (float4*)m; m += nv;
+    m += nv;  // spare
     t.a.xb_id = (float4*)m; m += nv;
     t.a.ub_id = (float4*)m; m += nv;
     t.a.dphat = (float*)m; m += nf;

@@ -269,23 +269,23 @@ struct AdjBuffers {
     float* dphat_s;
     float4* xb;              // (xbar, deltabar) of state n, sorted order of the step
     float4* ub;              // (ubar, alphabar partial)
-    float4* xbs;             // the same at the predicted state
-    float4* ubs;
-    float4* seed;            // (abar, drhobar) seeds of a VJP
+    float4* seed;            // (abar, drhobar) seeds of the VJP at the predicted state
+    float4* seed_n;          // seeds of the VJP at n
     float4* xb_id;           // adjoints between steps, indexed by upload id
     float4* ub_id;
     double* alpha_sum;
 };
-void launch_adj_dphat(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph,
-                      cudaStream_t st);
-void launch_adj_gather(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
-void launch_adj_scatter(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, cudaStream_t st);
+// one reversed step: reverse corrector, VJP at *, reverse predictor, VJP at n (three launches)
 void launch_adj_step(const AdjBuffers& a, const Buffers& b, int cur, const Geometry& g, const Phys& ph, float dt,
                      cudaStream_t st);
 void launch_adj_sum_alpha(const AdjBuffers& a, uint32_t n, double* out, cudaStream_t st);
 void launch_adj_load(const AdjBuffers& a, uint32_t n, const float* xbar, const float* ubar, const float* dbar,
                      cudaStream_t st);
 void launch_adj_store(const AdjBuffers& a, uint32_t n, float* xbar, float* ubar, float* dbar, cudaStream_t st);
+// copies of n elements of `count` arrays (16-byte elements where wide[k], else 4-byte), one launch
+constexpr int kTapeArrays = 8;
+void launch_tape_copy(const void* const* src, void* const* dst, const bool* wide, int count, uint32_t n,
+                      cudaStream_t st);
 
 // forces.cu
 enum ForceMode { kForcesOnly = 0, kPredict = 1, kCorrect = 2 };
