@@ -660,13 +660,32 @@ def run_batch(args):
     st0 = sim.stats(stream=stream)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
+        torch.cuda.synchronize()
+        clk.mark(True)
         ev0.record(stream)
         sim.step(args.steps, stream=stream)
         ev1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(False)
     t_b = ev0.elapsed_time(ev1) / 1e3
     st1 = sim.stats(stream=stream)
     inter_b = 2.0 * (st1["list_entries"] - st0["list_entries"])
+    # the same steps as one persistent kernel launch (grid-wide barriers between the phases)
+    sim.set_persistent(True)
+    sim.step(args.warmup, stream=stream)
+    torch.cuda.synchronize()
+    sp0 = sim.stats(stream=stream)
+    with ClockSampler(0) as clk_p:
+        torch.cuda.synchronize()
+        clk_p.mark(True)
+        ev0.record(stream)
+        sim.step(args.steps, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk_p.mark(False)
+    t_pk = ev0.elapsed_time(ev1) / 1e3
+    inter_pk = 2.0 * (sim.stats(stream=stream)["list_entries"] - sp0["list_entries"])
+    sim.set_persistent(False)
     # per-scene contexts, each tank launched on its own
     per = []
     for k, d in enumerate(b.scenes):
@@ -681,12 +700,16 @@ def run_batch(args):
     torch.cuda.synchronize()
     e0 = sum(ps.stats(stream=stream)["list_entries"] for ps in per)
     ps_steps = max(1, args.steps // 5)
-    ev0.record(stream)
-    for _ in range(ps_steps):
-        for ps in per:
-            ps.step(1, stream=stream)
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    with ClockSampler(0) as clk_s:
+        torch.cuda.synchronize()
+        clk_s.mark(True)
+        ev0.record(stream)
+        for _ in range(ps_steps):
+            for ps in per:
+                ps.step(1, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk_s.mark(False)
     t_p = ev0.elapsed_time(ev1) / 1e3
     inter_p = 2.0 * (sum(ps.stats(stream=stream)["list_entries"] for ps in per) - e0)
     line = {"metric": METRIC, "value": inter_b / t_b, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -697,8 +720,15 @@ def run_batch(args):
                                    "variants": dict(tuned, autotuned=True)},
             "particle_steps_per_s": b.n * args.steps / t_b,
             "per_scene_launches": {"value": inter_p / t_p, "ms_per_step": 1e3 * t_p / ps_steps,
-                                   "particle_steps_per_s": b.n * ps_steps / t_p, "steps": ps_steps},
-            "batched_speedup": (inter_b / t_b) / (inter_p / t_p), "clocks": clk.summary()}
+                                   "particle_steps_per_s": b.n * ps_steps / t_p, "steps": ps_steps,
+                                   "clocks": clk_s.summary()},
+            "persistent_kernel": {"value": inter_pk / t_pk, "ms_per_step": 1e3 * t_pk / args.steps,
+                                  "particle_steps_per_s": b.n * args.steps / t_pk, "steps": args.steps,
+                                  "launches": 1, "clocks": clk_p.summary(),
+                                  "note": "every phase of the step in one cooperative kernel with grid-wide "
+                                          "barriers, all steps of the timed region in one launch; same bits"},
+            "batched_speedup": (inter_b / t_b) / (inter_p / t_p), "gpu_launches": int(st1["kernels_per_step"] * args.steps),
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 

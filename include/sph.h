@@ -223,6 +223,19 @@ int sph_forces(sph_ctx* ctx, void* stream);
  * Conventions). */
 int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
 
+/* Step all scenes with one persistent kernel instead of the captured graph of
+ * per-phase kernels (on != 0), or back (0).  The persistent kernel runs every
+ * phase of the step (dt, hash, scan, scatter, reorder, list build, predictor
+ * pass, corrector pass) over all scenes' particles, with a grid-wide barrier
+ * between phases, for all the steps of one sph_step call: one cooperative
+ * launch (every block resident, so every barrier completes; it is launched as
+ * such each time, not replayed from a captured graph).  Same arithmetic as
+ * the graph path: the same results, to the bit.  Batching of independent scenes is not in the paper (its GPU
+ * section runs one scene per device); this is the single-launch form of the
+ * batched step.  Only with the list rebuilt every step and the default model
+ * (SPH_ERR_ARG otherwise).  Synchronises the device. */
+int sph_set_persistent(sph_ctx* ctx, int on);
+
 /* ---- differentiable run (reverse mode) --------------------------------
  * Loss L on the state after T steps; gradients w.r.t. the initial state and
  * the artificial-viscosity coefficient alpha.  The paper has no adjoint; it

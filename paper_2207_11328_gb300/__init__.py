@@ -81,6 +81,7 @@ _SIGS = {
     "sph_build_neighbors": [_vp, _vp],
     "sph_forces": [_vp, _vp],
     "sph_step": [_vp, ctypes.c_uint32, _vp],
+    "sph_set_persistent": [_vp, ctypes.c_int],
     "sph_step_profiled": [_vp, ctypes.c_uint32, _vp, _vp],
     "sph_download": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
     "sph_download_device": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
@@ -315,6 +316,11 @@ class Simulation:
 
     def step(self, nsteps=1, stream=None):
         _check(_lib().sph_step(self._h, int(nsteps), _stream_handle(stream)), "sph_step")
+
+    def set_persistent(self, on=True):
+        """Step with one persistent kernel launch per step() call (True) or the captured
+        graph of per-phase kernels (False); the same results to the bit."""
+        _check(_lib().sph_set_persistent(self._h, int(bool(on))), "sph_set_persistent")
 
     def autotune(self, stream=None):
         """Pick the fastest neighbour-build variant and force-kernel launch shape

@@ -19,7 +19,12 @@
 // The predictor (dt/2) and corrector (dt) updates of reading C6 are fused
 // into the epilogues of the two force passes; the corrector pass reduces
 // max |a|^2 per scene (warp reduction + one atomic) for the CFL dt (C7).
+#include <cooperative_groups.h>
+
 #include "forces_common.cuh"
+#include "pipeline.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace sphg {
 
@@ -87,12 +92,12 @@ __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const 
 // every step) before checking the displacement since the build.
 // (the forces-only pass keeps the |a|^2 reduction for dt0 live beside the sums: it gets
 // a looser register cap than the step's passes, so that no shape spills)
-template <int VISC, int MODE, int kBlock, int kMinBlocks, bool SKIN>
-__global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 + 2) / 3 : kMinBlocks) k_forces(
+template <int VISC, int MODE, bool SKIN>
+__device__ __forceinline__ void forces_body(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
-    const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
+    const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys& ph,
     int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
     uint32_t* __restrict__ ncount_x) {
     constexpr bool FILTER = SKIN && MODE != kCorrect;
@@ -339,6 +344,18 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
     }
 }
 
+template <int VISC, int MODE, int kBlock, int kMinBlocks, bool SKIN>
+__global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 + 2) / 3 : kMinBlocks) k_forces(
+    const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
+    float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
+    const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
+    const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
+    int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
+    uint32_t* __restrict__ ncount_x) {
+    forces_body<VISC, MODE, SKIN>(pos, vel, phat, io_pos, io_vel, io_phat, force_out, pinfo, nlist, ncount, scenes, dyn,
+                                  st, ph, acc_dt, pos_ref, nlist_x, ncount_x);
+}
+
 // Predictor update (reading C6) from forces already stored by a
 // forces-only pass at the same state: the same operations as the predictor
 // pass's epilogue, so the result is the same to the bit.  Used by the first
@@ -371,9 +388,10 @@ __global__ void k_predict_from_forces(const float4* __restrict__ pos, const floa
 
 // One thread per scene: dt for the coming step (reading C7), simulated
 // time, reset of the |a|^2 accumulator.
-__global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
-                     uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance, uint32_t rebuild_every,
-                     float trig2, uint32_t builds_inc) {
+__device__ __forceinline__ void dt_body(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn,
+                                        DevStatus* __restrict__ st, uint32_t n_scenes, double h, double cfl,
+                                        double dt_fixed, int advance, uint32_t rebuild_every, float trig2,
+                                        uint32_t builds_inc) {
     for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
         double dt;
         if (dt_fixed > 0.0) {
@@ -402,6 +420,65 @@ __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__
         } else {
             st->builds += builds_inc;
         }
+    }
+}
+
+__global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
+                     uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance, uint32_t rebuild_every,
+                     float trig2, uint32_t builds_inc) {
+    dt_body(scenes, dyn, st, n_scenes, h, cfl, dt_fixed, advance, rebuild_every, trig2, builds_inc);
+}
+
+// ---------------------------------------------------------------------
+// The whole step as one persistent kernel (batched scenes, north of the
+// per-kernel graph): every block runs each phase of the step over its share
+// of the particles (grid-stride loops), with a grid-wide barrier between
+// phases, for nsteps steps.  A cooperative launch keeps every block resident,
+// so the barriers always complete.  Phases and their arithmetic are the
+// kernels of the captured step (dt, hash, scan, scatter, reorder,
+// thread-per-particle list build, predictor pass, corrector pass), so the
+// result is the same to the bit.  List rebuilt every step, default model.
+// ---------------------------------------------------------------------
+// 4 resident blocks of 256 threads per SM (64 registers): measured faster than 3 (80
+// registers) and 2 (128): 12.5 / 13.9 / 16.3 ms per step on the 256-tank batch
+constexpr int kPersistMinBlocks = 4;
+template <int VISC>
+__global__ void __launch_bounds__(kPipeBlock, kPersistMinBlocks) k_step_persistent(const Buffers b, const Geometry g, const Phys ph,
+                                                                    int cur0, uint32_t nsteps) {
+    cg::grid_group grid = cg::this_grid();
+    const uint32_t nb = g.n_cells + 1;  // buckets: cells + the sentinel of removed particles
+    const uint32_t ntiles = (nb + kScanTile - 1) / kScanTile;
+    for (uint32_t s = 0; s < nsteps; ++s) {
+        const int cur = (cur0 + (int)s) & 1, nxt = cur ^ 1;
+        if (blockIdx.x == 0)
+            dt_body(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, 1, ph.rebuild_every,
+                    ph.skin_trig2, 1u);
+        hash_body(b.pos[cur], b.cell[cur], b.pinfo[cur], b.scenes, b.status, b.key, b.slot, b.count, g.n_cells);
+        grid.sync();
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) scan_reduce_tile(b.count, nb, b.bsum, t);
+        grid.sync();
+        if (blockIdx.x == 0) scan_bsums_body(b.bsum, ntiles);
+        grid.sync();
+        for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+            scan_down_tile(b.count, nb, b.bsum, b.start, b.status, t);
+        grid.sync();
+        scatter_body(b.key, b.slot, b.start, b.status, b.unsorted, nb);
+        grid.sync();
+        reorder_body(b.pos[cur], b.vel[cur], b.phat[cur], b.pinfo[cur], b.pid[cur], b.start, b.unsorted, b.scenes,
+                     g.n_cells, b.status, b.cell_nfluid, b.pos[nxt], b.vel[nxt], b.phat[nxt], b.cell[nxt],
+                     b.pinfo[nxt], b.pid[nxt]);
+        grid.sync();
+        build_tpp_body(b.pos[nxt], b.cell[nxt], b.pinfo[nxt], b.start, b.cell_nfluid, b.scenes, b.status, b.nlist,
+                       b.ncount, ph.R2_list, ph.max_neibs, ph.stride);
+        grid.sync();
+        forces_body<VISC, kPredict, false>(b.pos[nxt], b.vel[nxt], b.phat[nxt], b.pos_s, b.vel_s, b.phat_s, nullptr,
+                                           b.pinfo[nxt], b.nlist, b.ncount, b.scenes, b.dyn, b.status, ph, 0,
+                                           nullptr, nullptr, nullptr);
+        grid.sync();
+        forces_body<VISC, kCorrect, false>(b.pos_s, b.vel_s, b.phat_s, b.pos[nxt], b.vel[nxt], b.phat[nxt], nullptr,
+                                           b.pinfo[nxt], b.nlist, b.ncount, b.scenes, b.dyn, b.status, ph, 0,
+                                           nullptr, nullptr, nullptr);
+        grid.sync();
     }
 }
 
@@ -534,6 +611,33 @@ void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_
                int with_build) {
     k_dt<<<1, 256, 0, st>>>(b.scenes, b.dyn, b.status, g.n_scenes, ph.h_d, ph.cfl, ph.dt_fixed, advance_time,
                             ph.rebuild_every, ph.skin_trig2, with_build ? 1u : 0u);
+}
+
+// blocks of the persistent step kernel: all resident (a cooperative launch refuses more)
+template <int VISC>
+int persistent_grid() {
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_persistent<VISC>, kPipeBlock, 0) != cudaSuccess)
+        return 0;
+    return sms * per_sm;
+}
+
+cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g, const Phys& ph, uint32_t nsteps,
+                                   cudaStream_t st) {
+    const bool lam = ph.visc == SPH_VISC_LAMINAR;
+    const int grid = lam ? persistent_grid<SPH_VISC_LAMINAR>() : persistent_grid<SPH_VISC_ARTIFICIAL>();
+    if (grid <= 0) return cudaErrorLaunchFailure;
+    Buffers bb = b;
+    Geometry gg = g;
+    Phys pp = ph;
+    int c0 = cur;
+    uint32_t ns = nsteps;
+    void* args[] = {&bb, &gg, &pp, &c0, &ns};
+    const void* fn = lam ? (const void*)k_step_persistent<SPH_VISC_LAMINAR>
+                         : (const void*)k_step_persistent<SPH_VISC_ARTIFICIAL>;
+    return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kPipeBlock), args, 0, st);
 }
 
 void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {

@@ -52,6 +52,7 @@ struct sph_ctx {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // captured step, per buffer parity
     uint32_t graph_nodes = 0;
+    bool persistent = false;  // sph_set_persistent: one cooperative launch per sph_step call
     size_t staging_bytes = 0;
     std::vector<std::pair<char*, size_t>> canaries;  // checked build: (base, bytes) of guarded buffers
 };
@@ -736,6 +737,15 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
         CK(cudaGetLastError());
         c->need_dt0 = false;
     }
+    if (c->persistent) {
+        // the remaining steps as one cooperative launch of the persistent step kernel (launched
+        // directly: its grid-wide barriers need the cooperative launch itself, not a replay)
+        const uint32_t ns = nsteps - s;
+        CK(launch_step_persistent(c->b, c->cur, c->g, c->ph, ns, st));
+        c->cur = (int)((uint32_t)c->cur ^ (ns & 1u));
+        c->graph_nodes = 1;
+        return SPH_OK;
+    }
     if (!c->graph[c->cur]) {
         int rc = capture_graphs(c);
         if (rc) return rc;
@@ -744,6 +754,15 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
         CK(cudaGraphLaunch(c->graph[c->cur], st));
         if (!skin_mode(c)) c->cur ^= 1;
     }
+    return SPH_OK;
+}
+
+int sph_set_persistent(sph_ctx* c, int on) {
+    if (!c) return SPH_ERR_ARG;
+    if (on && (skin_mode(c) || c->ph.general)) return SPH_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    drop_graphs(c);
+    c->persistent = on != 0;
     return SPH_OK;
 }
 

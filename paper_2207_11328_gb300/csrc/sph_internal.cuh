@@ -310,6 +310,10 @@ void launch_force_rebuild(const Buffers& b, cudaStream_t st);
 // skin list counts its own rebuilds)
 void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_time, cudaStream_t st,
                int with_build = 1);
+// nsteps steps of the every-step pipeline (default model, no skin list) as one cooperative
+// launch of the persistent step kernel; buffer parity cur at the start, cur ^ (nsteps & 1) after
+cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g, const Phys& ph, uint32_t nsteps,
+                                   cudaStream_t st);
 // the predictor update from b.force (a forces-only pass at the same state, reading C6)
 void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 

@@ -86,3 +86,50 @@ def test_batch_with_a_skin_list_follows_the_every_step_run():
     assert np.max(np.abs(pa - pk)) < 1e-5 * b.dp
     f = b.ptype == 0
     assert np.max(np.abs(va[f] - vk[f])) <= 1e-4 * np.max(np.abs(va[f])) + 1e-6
+
+
+@pytest.mark.parametrize("case", ["batch", "box", "dam", "laminar_channel"])
+def test_persistent_step_kernel_equals_the_graph(case):
+    # the whole step as one persistent kernel (grid-wide barriers between the phases) gives
+    # the graph of per-phase kernels' results to the bit: states, per-scene dt and time,
+    # list counters; over step() calls of several lengths (odd and even buffer parities)
+    if case == "batch":
+        s = scenes.sloshing_batch(n_scenes=8, nmin=2000, nmax=12000, seed=81)
+    elif case == "box":
+        s = scenes.periodic_box(n_per_axis=16, jitter=0.2, seed=82)
+    elif case == "dam":
+        s = scenes.dam_break(dp=0.03)
+    else:
+        s = scenes.poiseuille(dp=1.0 / 16, nx=8, ny=16, nz=8)
+    g = sim_for(s)
+    p = sim_for(s)
+    p.set_persistent(True)
+    for n in (1, 4, 7, 2):
+        g.step(n)
+        p.step(n)
+    sg, sp = g.stats(), p.stats()
+    for k in ("n_active", "n_removed", "steps", "list_entries", "builds", "max_neibs_seen", "error_bits"):
+        assert sg[k] == sp[k], k
+    assert sp["kernels_per_step"] == 1
+    for a, b in zip(g.download(), p.download()):
+        assert np.array_equal(a, b)
+    dg, tg = g.scene_times()
+    dp_, tp = p.scene_times()
+    assert np.array_equal(dg, dp_) and np.array_equal(tg, tp)
+    # back to the graph: the context carries on from the persistent kernel's state
+    p.set_persistent(False)
+    g.step(3)
+    p.step(3)
+    for a, b in zip(g.download(), p.download()):
+        assert np.array_equal(a, b)
+
+
+def test_persistent_mode_refuses_a_skin_list_and_model_options():
+    from paper_2207_11328_gb300 import SphError
+    b = scenes.sloshing_batch(n_scenes=2, nmin=2000, nmax=3000, seed=83)
+    k = sim_for(b, rebuild_every=10, skin=0.3 * b.h, max_neibs=192)
+    with pytest.raises(SphError):
+        k.set_persistent(True)
+    m = sim_for(dataclasses.replace(b, kernel_type=1))
+    with pytest.raises(SphError):
+        m.set_persistent(True)
