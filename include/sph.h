@@ -223,6 +223,37 @@ int sph_forces(sph_ctx* ctx, void* stream);
  * Conventions). */
 int sph_step(sph_ctx* ctx, uint32_t nsteps, void* stream);
 
+/* Domain decomposition support (paper Section "Multi-GPU": each device holds
+ * its own particles plus copies of the neighbouring devices' particles near the
+ * boundary, the "halo").  Particles uploaded with an id >= n_owned are halo
+ * copies: they interact and are integrated like the others, but their forces
+ * are incomplete (their own neighbours beyond the halo are missing), so they
+ * are left out of the CFL time-step reduction.  UINT32_MAX (the default): no
+ * halo.  Synchronises the device. */
+int sph_set_owned(sph_ctx* ctx, uint32_t n_owned);
+
+/* Take dt (> 0, finite; else SPH_ERR_ARG) as the time step of the next step
+ * of every scene instead of the step's own CFL value (reading C7): a
+ * decomposed run agrees on one dt, the minimum of the devices' proposals
+ * (paper Section "The GPU in GPUSPH": the time step is a minimum over all
+ * particles, downloaded to the host).  Later steps return to their own CFL
+ * value.  Synchronises the device. */
+int sph_set_dt(sph_ctx* ctx, double dt);
+
+/* The CFL time step of the current state (reading C7, halo copies left out):
+ * one forces-only pass with its |a| reduction, without a step; scene 0's value
+ * into *dt (HOST).  For the first step of a decomposed run, whose dt is the
+ * minimum of every device's value before any step.  The step count and time
+ * are unchanged.  Synchronises `stream`. */
+int sph_cfl_dt(sph_ctx* ctx, double* dt, void* stream);
+
+/* The CFL time step the next step of scene 0 would take (reading C7: from the
+ * corrector-stage accelerations of the last step, halo copies left out),
+ * into *dt (HOST), without changing any state: a decomposed run reduces these
+ * proposals to their minimum and passes it to sph_set_dt.  Synchronises
+ * `stream`; SPH_ERR_STATE before an upload. */
+int sph_next_dt(sph_ctx* ctx, double* dt, void* stream);
+
 /* Step all scenes with one persistent kernel instead of the captured graph of
  * per-phase kernels (on != 0), or back (0).  The persistent kernel runs every
  * phase of the step (dt, hash, scan, scatter, reorder, list build, predictor

@@ -82,6 +82,10 @@ _SIGS = {
     "sph_forces": [_vp, _vp],
     "sph_step": [_vp, ctypes.c_uint32, _vp],
     "sph_set_persistent": [_vp, ctypes.c_int],
+    "sph_set_owned": [_vp, ctypes.c_uint32],
+    "sph_set_dt": [_vp, ctypes.c_double],
+    "sph_cfl_dt": [_vp, _vp, _vp],
+    "sph_next_dt": [_vp, _vp, _vp],
     "sph_step_profiled": [_vp, ctypes.c_uint32, _vp, _vp],
     "sph_download": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
     "sph_download_device": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
@@ -316,6 +320,26 @@ class Simulation:
 
     def step(self, nsteps=1, stream=None):
         _check(_lib().sph_step(self._h, int(nsteps), _stream_handle(stream)), "sph_step")
+
+    def set_owned(self, n_owned=0xFFFFFFFF):
+        """Particles with upload id >= n_owned are halo copies (left out of the CFL dt)."""
+        _check(_lib().sph_set_owned(self._h, int(n_owned)), "sph_set_owned")
+
+    def set_dt(self, dt):
+        """The time step of the next step (instead of its own CFL value)."""
+        _check(_lib().sph_set_dt(self._h, float(dt)), "sph_set_dt")
+
+    def cfl_dt(self, stream=None):
+        """CFL time step of the current state (halo copies left out), without a step."""
+        dt = ctypes.c_double()
+        _check(_lib().sph_cfl_dt(self._h, ctypes.byref(dt), _stream_handle(stream)), "sph_cfl_dt")
+        return dt.value
+
+    def next_dt(self, stream=None):
+        """CFL time step the next step would take (from the last step's accelerations)."""
+        dt = ctypes.c_double()
+        _check(_lib().sph_next_dt(self._h, ctypes.byref(dt), _stream_handle(stream)), "sph_next_dt")
+        return dt.value
 
     def set_persistent(self, on=True):
         """Step with one persistent kernel launch per step() call (True) or the captured

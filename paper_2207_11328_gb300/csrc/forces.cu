@@ -99,7 +99,7 @@ __device__ __forceinline__ void forces_body(
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys& ph,
     int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
-    uint32_t* __restrict__ ncount_x) {
+    uint32_t* __restrict__ ncount_x, const uint32_t* __restrict__ pid) {
     constexpr bool FILTER = SKIN && MODE != kCorrect;
     constexpr bool COMPACT = SKIN && MODE == kPredict;
     constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
@@ -326,7 +326,8 @@ __device__ __forceinline__ void forces_body(
             }
         }
         if (MODE == kCorrect || acc_dt) {
-            const float a2 = fluid_i ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
+            const float a2 = fluid_i && cfl_counts(ph, pid, i)
+                                 ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
             const uint32_t bits = __float_as_uint(a2);
             const unsigned mask = __activemask();
             const unsigned same = __match_any_sync(mask, s);
@@ -351,9 +352,9 @@ __global__ void __launch_bounds__(kBlock, MODE == kForcesOnly ? (kMinBlocks * 2 
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
     int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
-    uint32_t* __restrict__ ncount_x) {
+    uint32_t* __restrict__ ncount_x, const uint32_t* __restrict__ pid) {
     forces_body<VISC, MODE, SKIN>(pos, vel, phat, io_pos, io_vel, io_phat, force_out, pinfo, nlist, ncount, scenes, dyn,
-                                  st, ph, acc_dt, pos_ref, nlist_x, ncount_x);
+                                  st, ph, acc_dt, pos_ref, nlist_x, ncount_x, pid);
 }
 
 // Predictor update (reading C6) from forces already stored by a
@@ -388,24 +389,30 @@ __global__ void k_predict_from_forces(const float4* __restrict__ pos, const floa
 
 // One thread per scene: dt for the coming step (reading C7), simulated
 // time, reset of the |a|^2 accumulator.
+// The CFL time step of a scene from the largest |a|^2 of the last reduction (reading C7)
+__device__ __forceinline__ double cfl_dt_of(const SceneDev& sc, const SceneDyn& d, double h, double cfl,
+                                            double dt_fixed) {
+    if (dt_fixed > 0.0) return dt_fixed;
+    double dt = sc.dt_cap;
+    const double a2 = (double)__uint_as_float(d.amax2_bits);
+    if (a2 > 0.0) dt = fmin(dt, cfl * sqrt(h / sqrt(a2)));
+    return dt;
+}
+
 __device__ __forceinline__ void dt_body(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn,
                                         DevStatus* __restrict__ st, uint32_t n_scenes, double h, double cfl,
                                         double dt_fixed, int advance, uint32_t rebuild_every, float trig2,
                                         uint32_t builds_inc) {
+    const double dt_host = st->dt_next;  // the host's time step for this step (sph_set_dt), or <= 0
+    __syncthreads();
     for (uint32_t s = threadIdx.x; s < n_scenes; s += blockDim.x) {
-        double dt;
-        if (dt_fixed > 0.0) {
-            dt = dt_fixed;
-        } else {
-            dt = scenes[s].dt_cap;
-            const double a2 = (double)__uint_as_float(dyn[s].amax2_bits);
-            if (a2 > 0.0) dt = fmin(dt, cfl * sqrt(h / sqrt(a2)));
-        }
+        const double dt = dt_host > 0.0 ? dt_host : cfl_dt_of(scenes[s], dyn[s], h, cfl, dt_fixed);
         dyn[s].dt = (float)dt;
         dyn[s].dt_d = dt;
         if (advance) dyn[s].time += dt;
         dyn[s].amax2_bits = 0u;
     }
+    if (threadIdx.x == 0 && dt_host > 0.0) st->dt_next = 0.0;
     if (threadIdx.x == 0 && advance) {
         st->steps += 1ull;
         if (rebuild_every > 1) {
@@ -421,6 +428,12 @@ __device__ __forceinline__ void dt_body(const SceneDev* __restrict__ scenes, Sce
             st->builds += builds_inc;
         }
     }
+}
+
+// the CFL dt the next step of scene 0 would take, without changing any state
+__global__ void k_dt_peek(const SceneDev* __restrict__ scenes, const SceneDyn* __restrict__ dyn,
+                          DevStatus* __restrict__ st, double h, double cfl, double dt_fixed) {
+    if (threadIdx.x == 0) st->dt_peek = cfl_dt_of(scenes[0], dyn[0], h, cfl, dt_fixed);
 }
 
 __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st,
@@ -473,11 +486,11 @@ __global__ void __launch_bounds__(kPipeBlock, kPersistMinBlocks) k_step_persiste
         grid.sync();
         forces_body<VISC, kPredict, false>(b.pos[nxt], b.vel[nxt], b.phat[nxt], b.pos_s, b.vel_s, b.phat_s, nullptr,
                                            b.pinfo[nxt], b.nlist, b.ncount, b.scenes, b.dyn, b.status, ph, 0,
-                                           nullptr, nullptr, nullptr);
+                                           nullptr, nullptr, nullptr, b.pid[nxt]);
         grid.sync();
         forces_body<VISC, kCorrect, false>(b.pos_s, b.vel_s, b.phat_s, b.pos[nxt], b.vel[nxt], b.phat[nxt], nullptr,
                                            b.pinfo[nxt], b.nlist, b.ncount, b.scenes, b.dyn, b.status, ph, 0,
-                                           nullptr, nullptr, nullptr);
+                                           nullptr, nullptr, nullptr, b.pid[nxt]);
         grid.sync();
     }
 }
@@ -490,18 +503,18 @@ void launch_forces_s(const Buffers& b, int cur, const Geometry& g, const Phys& p
         case kForcesOnly:
             k_forces<VISC, kForcesOnly, B, MB, SKIN><<<grid, B, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr, nullptr, b.force, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, nullptr, nullptr, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, nullptr, nullptr, nullptr, b.pid[cur]);
             break;
         case kPredict:
             k_forces<VISC, kPredict, B, MB, SKIN><<<grid, B, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s, b.phat_s, nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, nullptr, b.nlist_x, b.ncount_x);
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, nullptr, b.nlist_x, b.ncount_x, b.pid[cur]);
             break;
         case kCorrect:  // a skin list: the exact list the predictor wrote
             k_forces<VISC, kCorrect, B, MB, SKIN><<<grid, B, 0, st>>>(
                 b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur],
                 SKIN ? b.nlist_x : b.nlist, SKIN ? b.ncount_x : b.ncount, b.scenes, b.dyn, b.status, ph, 0,
-                b.pos_ref, nullptr, nullptr);
+                b.pos_ref, nullptr, nullptr, b.pid[cur]);
             break;
     }
 }
@@ -638,6 +651,10 @@ cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g,
     const void* fn = lam ? (const void*)k_step_persistent<SPH_VISC_LAMINAR>
                          : (const void*)k_step_persistent<SPH_VISC_ARTIFICIAL>;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kPipeBlock), args, 0, st);
+}
+
+void launch_dt_peek(const Buffers& b, const Phys& ph, cudaStream_t st) {
+    k_dt_peek<<<1, 32, 0, st>>>(b.scenes, b.dyn, b.status, ph.h_d, ph.cfl, ph.dt_fixed);
 }
 
 void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {

@@ -75,7 +75,8 @@ __device__ __forceinline__ void finish_particle(uint32_t i, uint32_t s, const Sc
                                                 const float4& vi, bool fluid_i, const Acc& acc, float4* io_pos,
                                                 float4* io_vel, float* io_phat, float4* __restrict__ force_out,
                                                 SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys& ph,
-                                                int acc_dt, const float4* __restrict__ pos_ref) {
+                                                int acc_dt, const float4* __restrict__ pos_ref,
+                                                const uint32_t* __restrict__ pid) {
     if (MODE == kForcesOnly) {
         force_out[i] = make_float4(acc.ax, acc.ay, acc.az, acc.drho);
     } else {
@@ -128,7 +129,8 @@ __device__ __forceinline__ void finish_particle(uint32_t i, uint32_t s, const Sc
         }
     }
     if (MODE == kCorrect || acc_dt) {
-        const float a2 = fluid_i ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
+        const float a2 = fluid_i && cfl_counts(ph, pid, i)
+                             ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
         const uint32_t bits = __float_as_uint(a2);
         const unsigned mask = __activemask();
         const unsigned same = __match_any_sync(mask, s);

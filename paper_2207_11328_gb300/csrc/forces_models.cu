@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
     const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys ph,
     int acc_dt, int skin, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
-    uint32_t* __restrict__ ncount_x) {
+    uint32_t* __restrict__ ncount_x, const uint32_t* __restrict__ pid) {
     // skin list: the predictor (and sph_forces) filter by the cutoff; the predictor keeps the
     // pairs within it (the step's exact list) for the corrector, which reads that list as is
     const bool filter = skin && MODE != kCorrect;
@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(kModelBlock, 4) k_forces_m(
             ncount_x[i] = xf.n | (xb.n << 16);
         }
         finish_particle<MODE>(i, s, sc, pi, vi, fluid_i, acc, io_pos, io_vel, io_phat, force_out, dyn, st, ph,
-                              acc_dt, pos_ref);
+                              acc_dt, pos_ref, pid);
     }
     if (compact) {
         const uint32_t w = __reduce_add_sync(0xffffffffu, npairs);
@@ -250,18 +250,18 @@ void launch_m(const Buffers& b, int cur, const Geometry& g, const Phys& ph, Forc
         case kForcesOnly:
             k_forces_m<KT, VISC, kForcesOnly><<<grid, kModelBlock, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], nullptr, nullptr, nullptr, b.force, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, skin, nullptr, nullptr, nullptr);
+                b.ncount, b.scenes, b.dyn, b.status, ph, acc_dt, skin, nullptr, nullptr, nullptr, b.pid[cur]);
             break;
         case kPredict:
             k_forces_m<KT, VISC, kPredict><<<grid, kModelBlock, 0, st>>>(
                 b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s, b.phat_s, nullptr, b.pinfo[cur], b.nlist,
-                b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin, nullptr, b.nlist_x, b.ncount_x);
+                b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin, nullptr, b.nlist_x, b.ncount_x, b.pid[cur]);
             break;
         case kCorrect:
             k_forces_m<KT, VISC, kCorrect><<<grid, kModelBlock, 0, st>>>(  // a skin list: the predictor's exact list
                 b.pos_s, b.vel_s, b.phat_s, b.pos[cur], b.vel[cur], b.phat[cur], nullptr, b.pinfo[cur],
                 skin ? b.nlist_x : b.nlist, skin ? b.ncount_x : b.ncount, b.scenes, b.dyn, b.status, ph, 0, skin,
-                b.pos_ref, nullptr, nullptr);
+                b.pos_ref, nullptr, nullptr, b.pid[cur]);
             break;
     }
 }

@@ -560,6 +560,7 @@ int sph_create(const sph_params* p, sph_ctx** out) {
         ph.lam_x = (float)(5.0 * (nu / 3.0 + zeta) * ir0);
     }
     ph.max_neibs = p->max_neibs;
+    ph.n_owned = kAllOwned;
     ph.gamma_i = (int)gm;
     ph.build_variant = 0;
     ph.forces_variant = 1;
@@ -754,6 +755,49 @@ int sph_step(sph_ctx* c, uint32_t nsteps, void* stream) {
         CK(cudaGraphLaunch(c->graph[c->cur], st));
         if (!skin_mode(c)) c->cur ^= 1;
     }
+    return SPH_OK;
+}
+
+int sph_cfl_dt(sph_ctx* c, double* dt, void* stream) {
+    if (!c || !dt) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    // one forces-only pass with the |a|^2 reduction, then the dt of reading C7 (no time advance)
+    launch_forces(c->b, c->cur, c->g, c->ph, kForcesOnly, 1, st);
+    launch_dt(c->b, c->g, c->ph, 0, st, 0);
+    SceneDyn d0;
+    CK(cudaMemcpyAsync(&d0, c->b.dyn, sizeof(d0), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *dt = d0.dt_d;
+    DevStatus hs;
+    CK(cudaMemcpy(&hs, c->b.status, sizeof(hs), cudaMemcpyDeviceToHost));
+    return error_from_bits(hs.error_bits);
+}
+
+int sph_next_dt(sph_ctx* c, double* dt, void* stream) {
+    if (!c || !dt) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    cudaStream_t st = S(stream);
+    launch_dt_peek(c->b, c->ph, st);
+    double v = 0.0;
+    CK(cudaMemcpyAsync(&v, &c->b.status->dt_peek, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *dt = v;
+    return SPH_OK;
+}
+
+int sph_set_owned(sph_ctx* c, uint32_t n_owned) {
+    if (!c) return SPH_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    c->ph.n_owned = n_owned;
+    drop_graphs(c);  // captured launches carry the old parameters
+    return SPH_OK;
+}
+
+int sph_set_dt(sph_ctx* c, double dt) {
+    if (!c || !(dt > 0.0) || !std::isfinite(dt)) return SPH_ERR_ARG;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(&c->b.status->dt_next, &dt, sizeof(double), cudaMemcpyHostToDevice));
     return SPH_OK;
 }
 

@@ -117,6 +117,8 @@ struct DevStatus {
     unsigned long long interactions;  // pairs within the influence radius (counted passes)
     uint32_t maxdisp2_bits;  // skin list: max displacement^2 since the build (float bits)
     uint32_t builds;         // neighbour-list builds since upload (the upload's included)
+    double dt_next;          // > 0: the time step of the next step, set by the host (sph_set_dt), then cleared
+    double dt_peek;          // sph_next_dt: the CFL dt of scene 0 from the last |a| reduction
 };
 
 // upload validation bits
@@ -152,7 +154,15 @@ struct Phys {
     int visc_avg;            // SPH_AVG_*
     int ddiff;               // SPH_DDIFF_*
     float lam_u, lam_x;      // laminar models: a += (lam_u u_ij + lam_x (u.x/r^2) x_ij) m_j f avg/(r_i r_j)
+    uint32_t n_owned;        // particles with upload id >= n_owned are halo copies (sph_set_owned):
+                             //   left out of the CFL reduction; kAllOwned: none
 };
+constexpr uint32_t kAllOwned = 0xFFFFFFFFu;
+
+// whether particle i takes part in the CFL reduction (a halo copy's forces are incomplete)
+__device__ __forceinline__ bool cfl_counts(const Phys& ph, const uint32_t* __restrict__ pid, uint32_t i) {
+    return ph.n_owned == kAllOwned || pid[i] < ph.n_owned;
+}
 
 constexpr int kBuildVariants = 5;
 constexpr uint32_t kPosPad = 8;  // spare float4 entries after pos[k][cap - 1] (read, never used)
@@ -314,6 +324,8 @@ void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_
 // launch of the persistent step kernel; buffer parity cur at the start, cur ^ (nsteps & 1) after
 cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g, const Phys& ph, uint32_t nsteps,
                                    cudaStream_t st);
+// DevStatus.dt_peek = the CFL dt the next step of scene 0 would take (no state change)
+void launch_dt_peek(const Buffers& b, const Phys& ph, cudaStream_t st);
 // the predictor update from b.force (a forces-only pass at the same state, reading C6)
 void launch_predict_from_forces(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 
