@@ -254,6 +254,21 @@ int sph_cfl_dt(sph_ctx* ctx, double* dt, void* stream);
  * `stream`; SPH_ERR_STATE before an upload. */
 int sph_next_dt(sph_ctx* ctx, double* dt, void* stream);
 
+/* Run the neighbour-list build and the predictor pass as one kernel (on != 0)
+ * or as two (0): each thread writes its particle's list (the thread-per-
+ * particle build) and evaluates the predictor pass over it at once, while
+ * the list and the candidates it has just tested are in cache.  The same list
+ * and the same results, to the bit.  sph_autotune fuses them when that is at
+ * least 2% faster.  Only with the list rebuilt every step and the default model
+ * (SPH_ERR_ARG otherwise); the paper runs the two as separate commands
+ * (Section 3 "Code structure").  Synchronises the device. */
+int sph_set_fused_predict(sph_ctx* ctx, int on);
+
+/* The step options in use (outputs nullable): the fused build + predictor
+ * kernel (sph_set_fused_predict) and the persistent step kernel
+ * (sph_set_persistent). */
+int sph_get_step_options(sph_ctx* ctx, int* fused_predict, int* persistent);
+
 /* Step all scenes with one persistent kernel instead of the captured graph of
  * per-phase kernels (on != 0), or back (0).  The persistent kernel runs every
  * phase of the step (dt, hash, scan, scatter, reorder, list build, predictor
@@ -318,8 +333,10 @@ int sph_tape_generation(sph_ctx* ctx, uint64_t* gen);
  * force-kernel shape (64, 128 or 256 threads per block with at most 64
  * registers; 128 threads with at most 85 or 128) on the uploaded state, the
  * predictor and the corrector pass apart (3 timed launches each, CUDA events
- * on `stream`; the corrector runs on a scratch copy of the state), keeps the
- * fastest and re-captures the step graph on the next sph_step.  The
+ * on `stream`; the corrector runs on a scratch copy of the state), then the
+ * list build and the predictor pass fused against apart (every-step list,
+ * default model), keeps the fastest and re-captures the step graph on the
+ * next sph_step.  The
  * particle state and the next time step are as before the call (the list
  * counters include the timed builds).  Outputs (nullable): the build
  * variant and the predictor pass's shape (names: sph_build_variant_name,
@@ -350,8 +367,9 @@ const char* sph_forces_variant_name(int variant);
 /* Same work as sph_step, launched kernel by kernel (no graph) with CUDA
  * events recorded on `stream` between the launches; adds the elapsed
  * milliseconds of each phase to phase_ms[0..7]: 0 dt, 1 hash, 2 scan,
- * 3 scatter, 4 in-cell sort + reorder, 5 neighbour-list build,
- * 6 forces + predictor, 7 forces + corrector.  Synchronises after each
+ * 3 scatter, 4 in-cell sort + reorder, 5 neighbour-list build (with the
+ * predictor pass when they are fused, see sph_set_fused_predict),
+ * 6 forces + predictor (0 when fused), 7 forces + corrector.  Synchronises after each
  * step (measurement aid; sph_step is the production path). */
 int sph_step_profiled(sph_ctx* ctx, uint32_t nsteps, void* stream, double* phase_ms);
 

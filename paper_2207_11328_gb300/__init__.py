@@ -82,6 +82,8 @@ _SIGS = {
     "sph_forces": [_vp, _vp],
     "sph_step": [_vp, ctypes.c_uint32, _vp],
     "sph_set_persistent": [_vp, ctypes.c_int],
+    "sph_set_fused_predict": [_vp, ctypes.c_int],
+    "sph_get_step_options": [_vp, _vp, _vp],
     "sph_set_owned": [_vp, ctypes.c_uint32],
     "sph_set_dt": [_vp, ctypes.c_double],
     "sph_cfl_dt": [_vp, _vp, _vp],
@@ -340,6 +342,16 @@ class Simulation:
         dt = ctypes.c_double()
         _check(_lib().sph_next_dt(self._h, ctypes.byref(dt), _stream_handle(stream)), "sph_next_dt")
         return dt.value
+
+    def set_fused_predict(self, on=True):
+        """List build and predictor pass as one kernel (True) or two (False); same bits."""
+        _check(_lib().sph_set_fused_predict(self._h, int(bool(on))), "sph_set_fused_predict")
+
+    def step_options(self):
+        """{"fused_predict": bool, "persistent": bool} in use."""
+        f, p = ctypes.c_int(), ctypes.c_int()
+        _check(_lib().sph_get_step_options(self._h, ctypes.byref(f), ctypes.byref(p)), "sph_get_step_options")
+        return {"fused_predict": bool(f.value), "persistent": bool(p.value)}
 
     def set_persistent(self, on=True):
         """Step with one persistent kernel launch per step() call (True) or the captured

@@ -92,6 +92,270 @@ __device__ __forceinline__ bool fluid_pair(uint32_t e, const Central& ci, const 
 // every step) before checking the displacement since the build.
 // (the forces-only pass keeps the |a|^2 reduction for dt0 live beside the sums: it gets
 // a looser register cap than the step's passes, so that no shape spills)
+// One particle of a force pass (one iteration of the pass's particle loop): its pair sums
+// over its list and the epilogue of the pass (store, predictor or corrector update).
+__device__ __forceinline__ uint32_t ld_count_fresh(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// List chunk loads: through the read-only path, or (FRESH: the list was written earlier in
+// the same kernel, by this thread) through L2 only, coherent with those stores.
+template <bool FRESH>
+__device__ __forceinline__ uint2 ld_chunk(const uint2* p) {
+    if (!FRESH) return __ldg(p);
+    uint2 v;
+    asm volatile("ld.global.cg.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
+    return v;
+}
+
+template <int VISC, int MODE, bool SKIN, bool FRESH = false>
+__device__ __forceinline__ void particle_pass(
+    uint32_t i, uint32_t n, const float4* __restrict__ pos, const float4* __restrict__ vel,
+    const float* __restrict__ phat, float4* io_pos, float4* io_vel, float* io_phat, float4* __restrict__ force_out,
+    const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
+    const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys& ph,
+    int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
+    uint32_t* __restrict__ ncount_x, const uint32_t* __restrict__ pid, uint32_t& npairs, uint32_t cnt_fresh = 0) {
+    static_assert(!(FRESH && SKIN), "a list written in the same kernel is a list built at this step");
+    constexpr bool FILTER = SKIN && MODE != kCorrect;
+    constexpr bool COMPACT = SKIN && MODE == kPredict;
+    constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
+    constexpr bool RECOMP = !FILTER;  // P_j/rho_j^2 recomputed (see fluid_pair)
+    const uint32_t s = pinfo[i];
+    const SceneDev& sc = scenes[s];
+    const float4 pi = pos[i];
+    const float4 vi = vel[i];
+    const uint32_t cnt = FRESH ? cnt_fresh : ncount[i];
+    uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+    SPH_GUARD(nf + nb <= ph.max_neibs, st, nf = nb = 0)
+    const bool fluid_i = pi.w > 0.f;
+    const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
+    Acc acc{0.f, 0.f, 0.f, 0.f};
+    const size_t S = ph.stride;
+    const uint32_t kxb = exact_bnd_chunk(ph.max_neibs);
+    ChunkWriter xf{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x), S, i};
+    ChunkWriter xb{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x) + (size_t)kxb * S, S, i};
+    if (fluid_i && CHUNKED) {
+        const float phat_i = phat[i];
+        const float pic = sc.pi_coef;
+        const Central ci = central_of(pi, cx, cy, cz);
+        // full chunks: four pairs with no test between them (their gathers issue together);
+        // then the last chunk of each part (1 to 3 entries, the rest kMarker)
+#define SPH_PAIR(BND, e) fluid_pair<VISC, BND, false, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)
+#define SPH_OK_E(e) (((e) >> kCodeBits) < n)
+        const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;
+        uint32_t k = 0;
+        uint4 qn = make_uint4(0u, 0u, 0u, 0u);
+        if (nf >= 4) qn = __ldg(cp);
+        for (; k + 4 <= nf; k += 4, cp += S) {
+            const uint4 q = qn;
+            if (k + 8 <= nf) qn = __ldg(cp + S);  // the next full chunk, one iteration ahead
+            SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
+            SPH_PAIR(false, q.x);
+            SPH_PAIR(false, q.y);
+            SPH_PAIR(false, q.z);
+            SPH_PAIR(false, q.w);
+        }
+        do {
+            if (k >= nf) break;
+            const uint4 q = __ldg(cp);
+            SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nf || SPH_OK_E(q.y)) && (k + 2 >= nf || SPH_OK_E(q.z)), st, break)
+            SPH_PAIR(false, q.x);
+            if (k + 1 < nf) SPH_PAIR(false, q.y);
+            if (k + 2 < nf) SPH_PAIR(false, q.z);
+        } while (0);
+        cp = reinterpret_cast<const uint4*>(nlist) + (size_t)kxb * S + i;
+        for (k = 0; k + 4 <= nb; k += 4, cp += S) {
+            const uint4 q = __ldg(cp);
+            SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
+            SPH_PAIR(true, q.x);
+            SPH_PAIR(true, q.y);
+            SPH_PAIR(true, q.z);
+            SPH_PAIR(true, q.w);
+        }
+        do {
+            if (k >= nb) break;
+            const uint4 q = __ldg(cp);
+            SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nb || SPH_OK_E(q.y)) && (k + 2 >= nb || SPH_OK_E(q.z)), st, break)
+            SPH_PAIR(true, q.x);
+            if (k + 1 < nb) SPH_PAIR(true, q.y);
+            if (k + 2 < nb) SPH_PAIR(true, q.z);
+        } while (0);
+#undef SPH_PAIR
+#undef SPH_OK_E
+        acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
+        acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
+        acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
+        acc.drho *= ph.aF;
+    } else if (fluid_i) {
+        const float phat_i = phat[i];
+        const float pic = sc.pi_coef;
+        const Central ci = central_of(pi, cx, cy, cz);
+        // list chunks come from DRAM: two chunks (four entries) per iteration, loaded one
+        // iteration ahead so that their latency is not on the path to the gathers
+        const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;
+        uint32_t k = 0;
+// keep a pair of the exact list (COMPACT only)
+#define SPH_KEEP_F(e) if (COMPACT) xf.put(e);
+#define SPH_KEEP_B(e) if (COMPACT) xb.put(e);
+        uint2 an = make_uint2(0u, 0u), bn = make_uint2(0u, 0u);
+        if (nf >= 4) {
+            an = ld_chunk<FRESH>(lp);
+            bn = ld_chunk<FRESH>(lp + S);
+        }
+        for (; k + 4 <= nf; k += 4, lp += 2 * S) {
+            const uint2 a = an, b = bn;
+            if (k + 8 <= nf) {  // the next iteration's chunks (within the fluid part)
+                an = ld_chunk<FRESH>(lp + 2 * S);
+                bn = ld_chunk<FRESH>(lp + 3 * S);
+            }
+            SPH_GUARD((max(max(a.x, a.y), max(b.x, b.y)) >> kCodeBits) < n, st, break)
+            if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
+            if (fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
+            if (fluid_pair<VISC, false, FILTER, RECOMP>(b.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.x)
+            if (fluid_pair<VISC, false, FILTER, RECOMP>(b.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.y)
+        }
+        for (; k < nf; k += 2, lp += S) {
+            const uint2 a = ld_chunk<FRESH>(lp);
+            const bool two = k + 1 < nf;
+            SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
+            if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
+            if (two && fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
+        }
+        lp = reinterpret_cast<const uint2*>(nlist) + (size_t)(list_chunks(ph.max_neibs) - 1u) * S + i;
+        for (k = 0; k < nb; k += 2, lp -= S) {
+            const uint2 a = ld_chunk<FRESH>(lp);
+            const bool two = k + 1 < nb;
+            SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
+            if (fluid_pair<VISC, true, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.x)
+            if (two && fluid_pair<VISC, true, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.y)
+        }
+        acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
+        acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
+        acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
+        acc.drho *= ph.aF;
+    } else {
+        // boundary particle: continuity over its fluid neighbours, u_i = 0
+        const Central ci = central_of(pi, cx, cy, cz);
+        const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;  // list of the build
+        const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;  // chunked exact list
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+        uint2 q2 = make_uint2(0u, 0u);
+#pragma unroll 2
+        for (uint32_t k = 0; k < nf; ++k) {
+            uint32_t e;
+            if (CHUNKED) {
+                if ((k & 3u) == 0u) {
+                    q = __ldg(cp);
+                    cp += S;
+                }
+                e = (k & 3u) == 0u ? q.x : ((k & 3u) == 1u ? q.y : ((k & 3u) == 2u ? q.z : q.w));
+            } else {
+                if ((k & 1u) == 0u) {
+                    q2 = ld_chunk<FRESH>(lp);
+                    lp += S;
+                }
+                e = (k & 1u) ? q2.y : q2.x;
+            }
+            const uint32_t j = e >> kCodeBits;
+            SPH_GUARD(j < n, st, continue)
+            const float4 pj = pos[j];
+            const float4 vj = vel[j];
+            const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;
+            const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
+            const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
+            const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
+            if (FILTER) {
+                if (!(r2 < ph.R2)) continue;
+                ++npairs;
+            }
+            SPH_KEEP_F(e)
+            const float r = r2 * rsqrtf(r2);
+            const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
+            const float mF = pj.w * (t * t * t);
+            const float udx = -fmaf(vj.x, rx, fmaf(vj.y, ry, vj.z * rz));
+            acc.drho = fmaf(mF, udx, acc.drho);
+        }
+        acc.drho *= ph.aF;
+    }
+#undef SPH_KEEP_F
+#undef SPH_KEEP_B
+    if (COMPACT) {
+        xf.flush();
+        xb.flush();
+        ncount_x[i] = xf.n | (xb.n << 16);
+    }
+
+    // epilogue written out here rather than through finish_particle() of
+    // forces_common.cuh (same operations): measured 7 % faster in these kernels
+    if (MODE == kForcesOnly) {
+        force_out[i] = make_float4(acc.ax, acc.ay, acc.az, acc.drho);
+    } else {
+        const float dt = dyn[s].dt;
+        if (MODE == kPredict) {
+            const float hd = 0.5f * dt;
+            float4 po = pi, vo = vi;
+            vo.w = fmaf(hd * ph.inv_rho0, acc.drho, vi.w);
+            if (fluid_i) {
+                vo.x = fmaf(hd, acc.ax, vi.x);
+                vo.y = fmaf(hd, acc.ay, vi.y);
+                vo.z = fmaf(hd, acc.az, vi.z);
+                po.x = fmaf(hd, vi.x, pi.x);
+                po.y = fmaf(hd, vi.y, pi.y);
+                po.z = fmaf(hd, vi.z, pi.z);
+            }
+            io_pos[i] = po;
+            io_vel[i] = vo;
+            io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
+        } else {  // kCorrect: state n in io_*, overwritten by n+1
+            float4 po = io_pos[i], vo = io_vel[i];
+            const float un_x = vo.x, un_y = vo.y, un_z = vo.z;
+            vo.w = fmaf(dt * ph.inv_rho0, acc.drho, vo.w);
+            if (fluid_i) {
+                vo.x = fmaf(dt, acc.ax, un_x);
+                vo.y = fmaf(dt, acc.ay, un_y);
+                vo.z = fmaf(dt, acc.az, un_z);
+                const float hd = 0.5f * dt;
+                po.x = fmaf(hd, un_x + vo.x, po.x);
+                po.y = fmaf(hd, un_y + vo.y, po.y);
+                po.z = fmaf(hd, un_z + vo.z, po.z);
+            }
+            io_pos[i] = po;
+            io_vel[i] = vo;
+            io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
+            const float chk = po.x + po.y + po.z + vo.x + vo.y + vo.z + vo.w;
+            if (!isfinite(chk)) atomicOr(&st->error_bits, SPH_EBIT_NONFINITE);
+            if (SKIN) {
+                // the list (built with a skin) covers the cutoff while no particle has
+                // moved more than skin/2 since the build; the largest displacement
+                // decides the next rebuild (k_dt)
+                const float4 r0 = pos_ref[i];
+                const float dx = po.x - r0.x, dy = po.y - r0.y, dz = po.z - r0.z;
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (d2 > ph.skin_lim2) atomicOr(&st->error_bits, SPH_EBIT_SKIN);
+                const unsigned mk = __activemask();
+                const uint32_t m = __reduce_max_sync(mk, __float_as_uint(d2));
+                if ((threadIdx.x & 31) == (uint32_t)(__ffs(mk) - 1)) atomicMax(&st->maxdisp2_bits, m);
+            }
+        }
+    }
+    if (MODE == kCorrect || acc_dt) {
+        const float a2 = fluid_i && cfl_counts(ph, pid, i)
+                             ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
+        const uint32_t bits = __float_as_uint(a2);
+        const unsigned mask = __activemask();
+        const unsigned same = __match_any_sync(mask, s);
+        if (same == mask) {
+            const uint32_t m = __reduce_max_sync(mask, bits);
+            if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1) && m) atomicMax(&dyn[s].amax2_bits, m);
+        } else if (bits) {
+            atomicMax(&dyn[s].amax2_bits, bits);
+        }
+    }
+}
+
 template <int VISC, int MODE, bool SKIN>
 __device__ __forceinline__ void forces_body(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
@@ -100,245 +364,11 @@ __device__ __forceinline__ void forces_body(
     const SceneDev* __restrict__ scenes, SceneDyn* __restrict__ dyn, DevStatus* __restrict__ st, const Phys& ph,
     int acc_dt, const float4* __restrict__ pos_ref, uint32_t* __restrict__ nlist_x,
     uint32_t* __restrict__ ncount_x, const uint32_t* __restrict__ pid) {
-    constexpr bool FILTER = SKIN && MODE != kCorrect;
-    constexpr bool COMPACT = SKIN && MODE == kPredict;
-    constexpr bool CHUNKED = SKIN && MODE == kCorrect;  // nlist/ncount: the exact list in chunks
-    constexpr bool RECOMP = !FILTER;  // P_j/rho_j^2 recomputed (see fluid_pair)
     const uint32_t n = st->n_active;
     uint32_t npairs = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint32_t s = pinfo[i];
-        const SceneDev& sc = scenes[s];
-        const float4 pi = pos[i];
-        const float4 vi = vel[i];
-        const uint32_t cnt = ncount[i];
-        uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
-        SPH_GUARD(nf + nb <= ph.max_neibs, st, nf = nb = 0)
-        const bool fluid_i = pi.w > 0.f;
-        const float cx = sc.cell_f[0], cy = sc.cell_f[1], cz = sc.cell_f[2];
-        Acc acc{0.f, 0.f, 0.f, 0.f};
-        const size_t S = ph.stride;
-        const uint32_t kxb = exact_bnd_chunk(ph.max_neibs);
-        ChunkWriter xf{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x), S, i};
-        ChunkWriter xb{make_uint4(0u, 0u, 0u, 0u), 0u, reinterpret_cast<uint4*>(nlist_x) + (size_t)kxb * S, S, i};
-        if (fluid_i && CHUNKED) {
-            const float phat_i = phat[i];
-            const float pic = sc.pi_coef;
-            const Central ci = central_of(pi, cx, cy, cz);
-            // full chunks: four pairs with no test between them (their gathers issue together);
-            // then the last chunk of each part (1 to 3 entries, the rest kMarker)
-#define SPH_PAIR(BND, e) fluid_pair<VISC, BND, false, RECOMP>(e, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)
-#define SPH_OK_E(e) (((e) >> kCodeBits) < n)
-            const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;
-            uint32_t k = 0;
-            uint4 qn = make_uint4(0u, 0u, 0u, 0u);
-            if (nf >= 4) qn = __ldg(cp);
-            for (; k + 4 <= nf; k += 4, cp += S) {
-                const uint4 q = qn;
-                if (k + 8 <= nf) qn = __ldg(cp + S);  // the next full chunk, one iteration ahead
-                SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
-                SPH_PAIR(false, q.x);
-                SPH_PAIR(false, q.y);
-                SPH_PAIR(false, q.z);
-                SPH_PAIR(false, q.w);
-            }
-            do {
-                if (k >= nf) break;
-                const uint4 q = __ldg(cp);
-                SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nf || SPH_OK_E(q.y)) && (k + 2 >= nf || SPH_OK_E(q.z)), st, break)
-                SPH_PAIR(false, q.x);
-                if (k + 1 < nf) SPH_PAIR(false, q.y);
-                if (k + 2 < nf) SPH_PAIR(false, q.z);
-            } while (0);
-            cp = reinterpret_cast<const uint4*>(nlist) + (size_t)kxb * S + i;
-            for (k = 0; k + 4 <= nb; k += 4, cp += S) {
-                const uint4 q = __ldg(cp);
-                SPH_GUARD(SPH_OK_E(q.x) && SPH_OK_E(q.y) && SPH_OK_E(q.z) && SPH_OK_E(q.w), st, break)
-                SPH_PAIR(true, q.x);
-                SPH_PAIR(true, q.y);
-                SPH_PAIR(true, q.z);
-                SPH_PAIR(true, q.w);
-            }
-            do {
-                if (k >= nb) break;
-                const uint4 q = __ldg(cp);
-                SPH_GUARD(SPH_OK_E(q.x) && (k + 1 >= nb || SPH_OK_E(q.y)) && (k + 2 >= nb || SPH_OK_E(q.z)), st, break)
-                SPH_PAIR(true, q.x);
-                if (k + 1 < nb) SPH_PAIR(true, q.y);
-                if (k + 2 < nb) SPH_PAIR(true, q.z);
-            } while (0);
-#undef SPH_PAIR
-#undef SPH_OK_E
-            acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
-            acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
-            acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
-            acc.drho *= ph.aF;
-        } else if (fluid_i) {
-            const float phat_i = phat[i];
-            const float pic = sc.pi_coef;
-            const Central ci = central_of(pi, cx, cy, cz);
-            // list chunks come from DRAM: two chunks (four entries) per iteration, loaded one
-            // iteration ahead so that their latency is not on the path to the gathers
-            const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;
-            uint32_t k = 0;
-// keep a pair of the exact list (COMPACT only)
-#define SPH_KEEP_F(e) if (COMPACT) xf.put(e);
-#define SPH_KEEP_B(e) if (COMPACT) xb.put(e);
-            uint2 an = make_uint2(0u, 0u), bn = make_uint2(0u, 0u);
-            if (nf >= 4) {
-                an = __ldg(lp);
-                bn = __ldg(lp + S);
-            }
-            for (; k + 4 <= nf; k += 4, lp += 2 * S) {
-                const uint2 a = an, b = bn;
-                if (k + 8 <= nf) {  // the next iteration's chunks (within the fluid part)
-                    an = __ldg(lp + 2 * S);
-                    bn = __ldg(lp + 3 * S);
-                }
-                SPH_GUARD((max(max(a.x, a.y), max(b.x, b.y)) >> kCodeBits) < n, st, break)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(b.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.x)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(b.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(b.y)
-            }
-            for (; k < nf; k += 2, lp += S) {
-                const uint2 a = __ldg(lp);
-                const bool two = k + 1 < nf;
-                SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
-                if (fluid_pair<VISC, false, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.x)
-                if (two && fluid_pair<VISC, false, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_F(a.y)
-            }
-            lp = reinterpret_cast<const uint2*>(nlist) + (size_t)(list_chunks(ph.max_neibs) - 1u) * S + i;
-            for (k = 0; k < nb; k += 2, lp -= S) {
-                const uint2 a = __ldg(lp);
-                const bool two = k + 1 < nb;
-                SPH_GUARD((a.x >> kCodeBits) < n && (!two || (a.y >> kCodeBits) < n), st, break)
-                if (fluid_pair<VISC, true, FILTER, RECOMP>(a.x, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.x)
-                if (two && fluid_pair<VISC, true, FILTER, RECOMP>(a.y, ci, vi, phat_i, pos, vel, phat, sc.phat_coef, pic, ph, acc, npairs)) SPH_KEEP_B(a.y)
-            }
-            acc.ax = fmaf(ph.aF, acc.ax, ph.g[0]);
-            acc.ay = fmaf(ph.aF, acc.ay, ph.g[1]);
-            acc.az = fmaf(ph.aF, acc.az, ph.g[2]);
-            acc.drho *= ph.aF;
-        } else {
-            // boundary particle: continuity over its fluid neighbours, u_i = 0
-            const Central ci = central_of(pi, cx, cy, cz);
-            const uint2* lp = reinterpret_cast<const uint2*>(nlist) + i;  // list of the build
-            const uint4* cp = reinterpret_cast<const uint4*>(nlist) + i;  // chunked exact list
-            uint4 q = make_uint4(0u, 0u, 0u, 0u);
-            uint2 q2 = make_uint2(0u, 0u);
-#pragma unroll 2
-            for (uint32_t k = 0; k < nf; ++k) {
-                uint32_t e;
-                if (CHUNKED) {
-                    if ((k & 3u) == 0u) {
-                        q = __ldg(cp);
-                        cp += S;
-                    }
-                    e = (k & 3u) == 0u ? q.x : ((k & 3u) == 1u ? q.y : ((k & 3u) == 2u ? q.z : q.w));
-                } else {
-                    if ((k & 1u) == 0u) {
-                        q2 = __ldg(lp);
-                        lp += S;
-                    }
-                    e = (k & 1u) ? q2.y : q2.x;
-                }
-                const uint32_t j = e >> kCodeBits;
-                SPH_GUARD(j < n, st, continue)
-                const float4 pj = pos[j];
-                const float4 vj = vel[j];
-                const float rx = pick(e, ci.xm, ci.x0, ci.xp) - pj.x;
-                const float ry = pick(e >> 2, ci.ym, ci.y0, ci.yp) - pj.y;
-                const float rz = pick(e >> 4, ci.zm, ci.z0, ci.zp) - pj.z;
-                const float r2 = fmaxf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)), 1e-30f);
-                if (FILTER) {
-                    if (!(r2 < ph.R2)) continue;
-                    ++npairs;
-                }
-                SPH_KEEP_F(e)
-                const float r = r2 * rsqrtf(r2);
-                const float t = fminf(fmaf(r, ph.inv_h, -2.0f), 0.0f);
-                const float mF = pj.w * (t * t * t);
-                const float udx = -fmaf(vj.x, rx, fmaf(vj.y, ry, vj.z * rz));
-                acc.drho = fmaf(mF, udx, acc.drho);
-            }
-            acc.drho *= ph.aF;
-        }
-#undef SPH_KEEP_F
-#undef SPH_KEEP_B
-        if (COMPACT) {
-            xf.flush();
-            xb.flush();
-            ncount_x[i] = xf.n | (xb.n << 16);
-        }
-
-        // epilogue written out here rather than through finish_particle() of
-        // forces_common.cuh (same operations): measured 7 % faster in these kernels
-        if (MODE == kForcesOnly) {
-            force_out[i] = make_float4(acc.ax, acc.ay, acc.az, acc.drho);
-        } else {
-            const float dt = dyn[s].dt;
-            if (MODE == kPredict) {
-                const float hd = 0.5f * dt;
-                float4 po = pi, vo = vi;
-                vo.w = fmaf(hd * ph.inv_rho0, acc.drho, vi.w);
-                if (fluid_i) {
-                    vo.x = fmaf(hd, acc.ax, vi.x);
-                    vo.y = fmaf(hd, acc.ay, vi.y);
-                    vo.z = fmaf(hd, acc.az, vi.z);
-                    po.x = fmaf(hd, vi.x, pi.x);
-                    po.y = fmaf(hd, vi.y, pi.y);
-                    po.z = fmaf(hd, vi.z, pi.z);
-                }
-                io_pos[i] = po;
-                io_vel[i] = vo;
-                io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
-            } else {  // kCorrect: state n in io_*, overwritten by n+1
-                float4 po = io_pos[i], vo = io_vel[i];
-                const float un_x = vo.x, un_y = vo.y, un_z = vo.z;
-                vo.w = fmaf(dt * ph.inv_rho0, acc.drho, vo.w);
-                if (fluid_i) {
-                    vo.x = fmaf(dt, acc.ax, un_x);
-                    vo.y = fmaf(dt, acc.ay, un_y);
-                    vo.z = fmaf(dt, acc.az, un_z);
-                    const float hd = 0.5f * dt;
-                    po.x = fmaf(hd, un_x + vo.x, po.x);
-                    po.y = fmaf(hd, un_y + vo.y, po.y);
-                    po.z = fmaf(hd, un_z + vo.z, po.z);
-                }
-                io_pos[i] = po;
-                io_vel[i] = vo;
-                io_phat[i] = eos_phat(vo.w, ph, sc.phat_coef);
-                const float chk = po.x + po.y + po.z + vo.x + vo.y + vo.z + vo.w;
-                if (!isfinite(chk)) atomicOr(&st->error_bits, SPH_EBIT_NONFINITE);
-                if (SKIN) {
-                    // the list (built with a skin) covers the cutoff while no particle has
-                    // moved more than skin/2 since the build; the largest displacement
-                    // decides the next rebuild (k_dt)
-                    const float4 r0 = pos_ref[i];
-                    const float dx = po.x - r0.x, dy = po.y - r0.y, dz = po.z - r0.z;
-                    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                    if (d2 > ph.skin_lim2) atomicOr(&st->error_bits, SPH_EBIT_SKIN);
-                    const unsigned mk = __activemask();
-                    const uint32_t m = __reduce_max_sync(mk, __float_as_uint(d2));
-                    if ((threadIdx.x & 31) == (uint32_t)(__ffs(mk) - 1)) atomicMax(&st->maxdisp2_bits, m);
-                }
-            }
-        }
-        if (MODE == kCorrect || acc_dt) {
-            const float a2 = fluid_i && cfl_counts(ph, pid, i)
-                                 ? fmaf(acc.ax, acc.ax, fmaf(acc.ay, acc.ay, acc.az * acc.az)) : 0.f;
-            const uint32_t bits = __float_as_uint(a2);
-            const unsigned mask = __activemask();
-            const unsigned same = __match_any_sync(mask, s);
-            if (same == mask) {
-                const uint32_t m = __reduce_max_sync(mask, bits);
-                if ((threadIdx.x & 31) == (uint32_t)(__ffs(mask) - 1) && m) atomicMax(&dyn[s].amax2_bits, m);
-            } else if (bits) {
-                atomicMax(&dyn[s].amax2_bits, bits);
-            }
-        }
-    }
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        particle_pass<VISC, MODE, SKIN>(i, n, pos, vel, phat, io_pos, io_vel, io_phat, force_out, pinfo, nlist, ncount,
+                                        scenes, dyn, st, ph, acc_dt, pos_ref, nlist_x, ncount_x, pid, npairs);
     if (SKIN && MODE == kPredict) {
         const uint32_t w = __reduce_add_sync(0xffffffffu, npairs);
         if ((threadIdx.x & 31) == 0 && w) atomicAdd(&st->interactions, (unsigned long long)w);
@@ -440,6 +470,34 @@ __global__ void k_dt(const SceneDev* __restrict__ scenes, SceneDyn* __restrict__
                      uint32_t n_scenes, double h, double cfl, double dt_fixed, int advance, uint32_t rebuild_every,
                      float trig2, uint32_t builds_inc) {
     dt_body(scenes, dyn, st, n_scenes, h, cfl, dt_fixed, advance, rebuild_every, trig2, builds_inc);
+}
+
+// ---------------------------------------------------------------------
+// The neighbour build and the predictor pass in one kernel: each thread writes
+// its particle's list (the thread-per-particle build) and evaluates the
+// predictor pass over it at once, while the list and the candidates it has
+// just loaded are in cache; no separate pass re-reads the list.  The same
+// list and, pair for pair in the same order, the same sums and update as the
+// two kernels.  List rebuilt every step (no skin), default model.
+// ---------------------------------------------------------------------
+template <int VISC>
+__global__ void __launch_bounds__(kPipeBlock, 4) k_build_predict(const Buffers b, int cur, const Phys ph) {
+    DevStatus* st = b.status;
+    const uint32_t n = st->n_active;
+    const uint32_t r2lim = __float_as_uint(ph.R2_list) - 1u;
+    uint32_t npairs = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        uint32_t nfound;
+        const uint32_t nent = build_particle(i, b.pos[cur], b.cell[cur], b.pinfo[cur], b.start, b.cell_nfluid, b.scenes,
+                                             b.nlist, b.ncount, r2lim, ph.max_neibs, ph.stride, &nfound, st, n);
+        build_stats(st, nfound, nent, ph.max_neibs, __activemask());
+        asm volatile("" ::: "memory");  // the list stores above precede its loads below
+        const uint32_t cnt = ld_count_fresh(b.ncount + i);
+        particle_pass<VISC, kPredict, false, true>(i, n, b.pos[cur], b.vel[cur], b.phat[cur], b.pos_s, b.vel_s,
+                                                   b.phat_s, nullptr, b.pinfo[cur], b.nlist, b.ncount, b.scenes,
+                                                   b.dyn, st, ph, 0, nullptr, nullptr, nullptr, b.pid[cur], npairs,
+                                                   cnt);
+    }
 }
 
 // ---------------------------------------------------------------------
@@ -651,6 +709,14 @@ cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g,
     const void* fn = lam ? (const void*)k_step_persistent<SPH_VISC_LAMINAR>
                          : (const void*)k_step_persistent<SPH_VISC_ARTIFICIAL>;
     return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kPipeBlock), args, 0, st);
+}
+
+void launch_build_predict(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st) {
+    const unsigned grid = g.cap ? (g.cap + kPipeBlock - 1) / kPipeBlock : 1;
+    if (ph.visc == SPH_VISC_LAMINAR)
+        k_build_predict<SPH_VISC_LAMINAR><<<grid, kPipeBlock, 0, st>>>(b, cur, ph);
+    else
+        k_build_predict<SPH_VISC_ARTIFICIAL><<<grid, kPipeBlock, 0, st>>>(b, cur, ph);
 }
 
 void launch_dt_peek(const Buffers& b, const Phys& ph, cudaStream_t st) {

@@ -147,6 +147,7 @@ struct Phys {
     int forces_variant;      // launch shape of the forces-only and predictor passes (autotuned), see
                              //   forces_variant_name
     int forces_variant_c;    // launch shape of the corrector pass (autotuned on its own)
+    int fuse_predict;        // the list build and the predictor pass as one kernel (autotuned)
     // model options (Table 1); general != 0 selects the kernels of forces_models.cu
     int general;
     int kernel_type;         // SPH_KERNEL_*: F = aF f(q)
@@ -324,6 +325,8 @@ void launch_dt(const Buffers& b, const Geometry& g, const Phys& ph, int advance_
 // launch of the persistent step kernel; buffer parity cur at the start, cur ^ (nsteps & 1) after
 cudaError_t launch_step_persistent(const Buffers& b, int cur, const Geometry& g, const Phys& ph, uint32_t nsteps,
                                    cudaStream_t st);
+// the list build and the predictor pass as one kernel (every-step list, default model)
+void launch_build_predict(const Buffers& b, int cur, const Geometry& g, const Phys& ph, cudaStream_t st);
 // DevStatus.dt_peek = the CFL dt the next step of scene 0 would take (no state change)
 void launch_dt_peek(const Buffers& b, const Phys& ph, cudaStream_t st);
 // the predictor update from b.force (a forces-only pass at the same state, reading C6)

@@ -133,3 +133,39 @@ def test_persistent_mode_refuses_a_skin_list_and_model_options():
     m = sim_for(dataclasses.replace(b, kernel_type=1))
     with pytest.raises(SphError):
         m.set_persistent(True)
+
+
+@pytest.mark.parametrize("case", ["batch", "box", "dam", "laminar_channel"])
+def test_fused_build_and_predictor_equal_the_two_kernels(case):
+    # the list build and the predictor pass as one kernel: the same list, states, dt and
+    # counters as the two kernels, to the bit
+    if case == "batch":
+        s = scenes.sloshing_batch(n_scenes=8, nmin=2000, nmax=12000, seed=84)
+    elif case == "box":
+        s = scenes.periodic_box(n_per_axis=16, jitter=0.2, seed=85)
+    elif case == "dam":
+        s = scenes.dam_break(dp=0.03)
+    else:
+        s = scenes.poiseuille(dp=1.0 / 16, nx=8, ny=16, nz=8)
+    a = sim_for(s)
+    f = sim_for(s)
+    a.set_fused_predict(False)
+    f.set_fused_predict(True)
+    assert f.step_options()["fused_predict"] and not a.step_options()["fused_predict"]
+    for n in (1, 5, 2):
+        a.step(n)
+        f.step(n)
+    sa, sf = a.stats(), f.stats()
+    for k in ("n_active", "steps", "list_entries", "builds", "max_neibs_seen", "error_bits"):
+        assert sa[k] == sf[k], k
+    for x, y in zip(a.download(), f.download()):
+        assert np.array_equal(x, y)
+    ca, ia = a.download_neighbors()
+    cf, if_ = f.download_neighbors()
+    assert np.array_equal(ca, cf) and np.array_equal(ia, if_)
+    # step_profiled (kernel by kernel) runs the fused kernel too
+    a.step_profiled(2)
+    ph = f.step_profiled(2)
+    assert ph["forces_predict"] == 0.0 and ph["build"] > 0.0
+    for x, y in zip(a.download(), f.download()):
+        assert np.array_equal(x, y)
