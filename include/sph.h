@@ -397,6 +397,16 @@ int sph_download_forces(sph_ctx* ctx, uint32_t n, float* acc, float* drho, void*
  * HOST arrays; synchronises. */
 int sph_download_neighbors(sph_ctx* ctx, uint32_t n, uint32_t* counts, uint32_t* ids, void* stream);
 
+/* The neighbour lists of m sampled particles, by upload id: sample[0..m) (HOST)
+ * upload ids; counts m*2 (fluid, boundary neighbours of sample[k]), ids
+ * m*max_neibs upload ids in the layout of sph_download_neighbors, row k for
+ * sample[k] (HOST outputs).  For checking a few lists of a state too large to
+ * download whole.  Allocates per-call device staging (4 B per uploaded
+ * particle plus the outputs) and frees it; SPH_ERR_ARG for an id out of
+ * range (the other rows are still written).  Synchronises `stream`. */
+int sph_download_neighbors_of(sph_ctx* ctx, uint32_t m, const uint32_t* sample, uint32_t* counts, uint32_t* ids,
+                              void* stream);
+
 /* Same result as sph_download_neighbors, without allocating device memory.
  * The paper has no counterpart: this entry point exists for callers that
  * must not call cudaMalloc/cudaFree while they run, e.g. a process whose

@@ -78,6 +78,8 @@ def _configure(lib):
     lib.ora_eos.argtypes = [P, ctypes.c_double]
     lib.ora_neighbors.restype = ctypes.c_int64
     lib.ora_neighbors.argtypes = [P, ctypes.c_int, dp_, ctypes.c_int, ctypes.c_int64, i64p, i32p]
+    lib.ora_neighbors_sample.restype = ctypes.c_int64
+    lib.ora_neighbors_sample.argtypes = [P, ctypes.c_int, dp_, ctypes.c_int, i32p, ctypes.c_int64, i64p, i32p]
     lib.ora_rhs.restype = ctypes.c_int
     lib.ora_rhs.argtypes = [P, ctypes.c_int, dp_, dp_, dp_, dp_, u8p, dp_, dp_, dp_]
     lib.ora_rhs_sample.restype = ctypes.c_int
@@ -180,6 +182,26 @@ def neighbors(p: Params, pos, brute=False):
         tot = lib.ora_neighbors(ctypes.byref(p), n, pp, int(brute), cap,
                                 off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                 idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+        if tot >= 0:
+            return off, idx[:tot].copy()
+        cap = -tot
+
+
+def neighbors_sample(p: Params, pos, sample):
+    """CSR neighbour sets of the particles in `sample` only (searched among all):
+    offsets int64[len(sample)+1], indices int32[...], ascending per particle."""
+    lib = _load()
+    pos, pp = _d(pos)
+    n = pos.shape[0]
+    smp = np.ascontiguousarray(sample, np.int32)
+    off = np.zeros(len(smp) + 1, np.int64)
+    cap = max(1, len(smp) * 128)
+    while True:
+        idx = np.zeros(cap, np.int32)
+        tot = lib.ora_neighbors_sample(ctypes.byref(p), n, pp, len(smp),
+                                       smp.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), cap,
+                                       off.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
         if tot >= 0:
             return off, idx[:tot].copy()
         cap = -tot

@@ -573,6 +573,43 @@ int64_t ora_neighbors(const ora_params* P, int n, const double* x, int brute, in
     return tot;
 }
 
+/* Neighbour sets of a sample of particles only (indices sidx[0..ns)), searched
+ * among all n particles with the same binning as ora_neighbors (Section 2.3:
+ * candidates in the neighbouring cells, reading C9: 0 < r < R).  CSR output:
+ * off[0..ns], idx[...] (cap entries at most; returns the total, negated when it
+ * exceeds cap). */
+int64_t ora_neighbors_sample(const ora_params* P, int n, const double* x, int ns, const int32_t* sidx, int64_t cap,
+                             int64_t* off, int32_t* idx) {
+    if (!P || n < 0 || ns < 0) return -1;
+    Bins B;
+    const bool have_bins = make_bins(*P, n, x, B);
+    const double R2 = radius(*P) * radius(*P);
+    std::vector<int32_t> nb;
+    int64_t tot = 0;
+    off[0] = 0;
+    for (int s = 0; s < ns; ++s) {
+        const int i = sidx[s];
+        if (have_bins) {
+            neighbors_of(*P, x, B, i, nb);
+        } else {
+            nb.clear();
+            for (int j = 0; j < n; ++j) {
+                if (j == i) continue;
+                double d[3];
+                separation(*P, x + 3 * i, x + 3 * j, d);
+                double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (r2 > 0.0 && r2 < R2) nb.push_back(j);
+            }
+        }
+        for (size_t k = 0; k < nb.size(); ++k) {
+            if (tot + (int64_t)k < cap) idx[tot + (int64_t)k] = nb[k];
+        }
+        tot += (int64_t)nb.size();
+        off[s + 1] = tot;
+    }
+    return tot > cap ? -tot : tot;
+}
+
 /* Time derivatives of all particles at the given state.  a: n*3, drho: n,
  * mag: n*2 summed term magnitudes (nullable, see particle_rhs). */
 int ora_rhs(const ora_params* P, int n, const double* x, const double* u, const double* delta,

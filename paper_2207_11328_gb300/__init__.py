@@ -94,6 +94,7 @@ _SIGS = {
     "sph_download_forces": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
     "sph_download_neighbors": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
     "sph_download_neighbors_noalloc": [_vp, ctypes.c_uint32, _vp, _vp, _vp],
+    "sph_download_neighbors_of": [_vp, ctypes.c_uint32, _vp, _vp, _vp, _vp],
     "sph_get_stats": [_vp, ctypes.POINTER(Stats), _vp],
     "sph_get_scene_times": [_vp, _vp, _vp, _vp],
     "sph_clear_error": [_vp, _vp],
@@ -300,6 +301,16 @@ class Simulation:
         ids = np.empty((n, mn), np.uint32)
         _check(_lib().sph_download_neighbors(self._h, n, _ptr(counts), _ptr(ids), _stream_handle(stream)),
                "sph_download_neighbors")
+        return counts, ids
+
+    def download_neighbors_of(self, sample, stream=None):
+        """Lists of the particles with upload ids `sample`: (counts[m,2], ids[m,max_neibs])."""
+        smp = np.ascontiguousarray(sample, np.uint32)
+        m, mn = smp.shape[0], self.params.max_neibs
+        counts = np.empty((m, 2), np.uint32)
+        ids = np.empty((m, mn), np.uint32)
+        _check(_lib().sph_download_neighbors_of(self._h, m, _ptr(smp), _ptr(counts), _ptr(ids),
+                                                _stream_handle(stream)), "sph_download_neighbors_of")
         return counts, ids
 
     def download_neighbors_noalloc(self, stream=None):

@@ -262,6 +262,35 @@ __global__ void k_download_neighbors(const uint32_t* __restrict__ nlist, const u
     }
 }
 
+// the lists of a sample of particles: slot[id] = the sample position of upload id, or ~0
+__global__ void k_download_neighbors_of(const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount,
+                                        const uint32_t* __restrict__ pid, const DevStatus* __restrict__ st,
+                                        const uint32_t* __restrict__ slot, uint32_t n_up, uint32_t max_neibs,
+                                        uint32_t stride, uint32_t* __restrict__ counts, uint32_t* __restrict__ ids) {
+    const uint32_t n = st->n_active;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t id = pid[i];
+        if (id >= n_up) continue;
+        const uint32_t s = slot[id];
+        if (s == 0xFFFFFFFFu) continue;
+        const uint32_t cnt = ncount[i];
+        const uint32_t nf = cnt & 0xffffu, nb = cnt >> 16;
+        counts[2 * (size_t)s] = nf;
+        counts[2 * (size_t)s + 1] = nb;
+        uint32_t* out = ids + (size_t)s * max_neibs;
+        for (uint32_t k = 0; k < nf; ++k) out[k] = pid[nlist[list_fluid_word(k, i, stride)] >> kCodeBits];
+        for (uint32_t k = 0; k < nb; ++k) out[nf + k] = pid[nlist[list_bnd_word(k, i, stride, max_neibs)] >> kCodeBits];
+    }
+}
+
+__global__ void k_fill_slots(const uint32_t* __restrict__ sample, uint32_t m, uint32_t n_up, uint32_t* __restrict__ slot,
+                             uint32_t* __restrict__ bad) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        if (sample[k] < n_up) slot[sample[k]] = k;
+        else atomicOr(bad, 1u);
+    }
+}
+
 int scene_from(const sph_params& p, const double origin[3], const double size[3], uint32_t periodic, double c0,
                uint32_t cell_offset, SceneDev& s, uint64_t& ncells) {
     // cells of side >= the list radius (influence radius + skin in rebuild-every-k mode)
@@ -1424,6 +1453,49 @@ int sph_download_neighbors(sph_ctx* c, uint32_t n, uint32_t* counts, uint32_t* i
         return SPH_ERR_CUDA;
     }
     return SPH_OK;
+}
+
+int sph_download_neighbors_of(sph_ctx* c, uint32_t m, const uint32_t* sample, uint32_t* counts, uint32_t* ids,
+                              void* stream) {
+    if (!c || (m && (!sample || !counts || !ids))) return SPH_ERR_ARG;
+    if (!c->uploaded) return SPH_ERR_STATE;
+    if (m == 0) return SPH_OK;
+    cudaStream_t st = S(stream);
+    const uint32_t n_up = c->n_uploaded;
+    const size_t nid = (size_t)m * c->p.max_neibs;
+    // one staging block: slot map (n_up), sample (m), counts (2m), ids (m*max_neibs), a flag
+    const size_t bytes = sizeof(uint32_t) * ((size_t)n_up + 3 * (size_t)m + nid + 1);
+    uint32_t* blk = nullptr;
+    CK(cudaMalloc(&blk, bytes));
+    uint32_t* slot = blk;
+    uint32_t* dsmp = slot + n_up;
+    uint32_t* dcnt = dsmp + m;
+    uint32_t* dids = dcnt + 2 * (size_t)m;
+    uint32_t* dbad = dids + nid;
+    cudaError_t e = cudaMemsetAsync(slot, 0xFF, sizeof(uint32_t) * n_up, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, sizeof(uint32_t) * (2 * (size_t)m), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dids, 0xFF, sizeof(uint32_t) * nid, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dbad, 0, sizeof(uint32_t), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dsmp, sample, sizeof(uint32_t) * m, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        k_fill_slots<<<grid_for(m, 256), 256, 0, st>>>(dsmp, m, n_up, slot, dbad);
+        k_download_neighbors_of<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.nlist, c->b.ncount, c->b.pid[c->cur],
+                                                                          c->b.status, slot, n_up, c->p.max_neibs,
+                                                                          c->ph.stride, dcnt, dids);
+        e = cudaGetLastError();
+    }
+    uint32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, dcnt, sizeof(uint32_t) * 2 * (size_t)m, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ids, dids, sizeof(uint32_t) * nid, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, dbad, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    const cudaError_t es = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = es;
+    cudaFree(blk);
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "sph: sph_download_neighbors_of failed: %s\n", cudaGetErrorString(e));
+        return SPH_ERR_CUDA;
+    }
+    return bad ? SPH_ERR_ARG : SPH_OK;
 }
 
 // ---------------------------------------------------------------------

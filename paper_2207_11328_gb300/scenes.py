@@ -306,3 +306,9 @@ def seeded_directions(n, count, seed=SEED_BASE + 3):
 def seeded_normal(shape, scale, seed):
     rng = np.random.Generator(np.random.PCG64(seed))
     return rng.normal(0.0, scale, size=shape)
+
+
+def seeded_uniform(shape, lo, hi, seed):
+    """Seeded U[lo, hi) samples (float64), e.g. to jitter positions of a lattice."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return rng.uniform(lo, hi, size=shape)

@@ -139,3 +139,36 @@ def compare_neighbor_sets_sample(scene, sample, counts, ids, band=1e-6):
                                         f"oracle-gpu {sorted(set(sure.tolist()) - g)}"
         total += len(sure)
     return total
+
+
+def compare_neighbor_sets_of(scene, sample, counts, ids, band=1e-6):
+    """GPU lists of the sampled particles (rows of sph_download_neighbors_of) against the
+    oracle's sampled search, excluding pairs within band*h of the cutoff.  Returns the
+    number of compared pairs."""
+    R = scene.kernel_radius * scene.h
+    p_out = oracle.params(scene, kernel_radius=(R + band * scene.h) / scene.h)
+    off, idx = oracle.neighbors_sample(p_out, scene.pos, sample)
+    fluid = scene.ptype == 0
+    size = np.array(scene.size)
+    total = 0
+    for k, i in enumerate(sample):
+        js = idx[off[k]:off[k + 1]]
+        d = scene.pos[i][None, :] - scene.pos[js]
+        for a in range(3):
+            if (scene.periodic >> a) & 1:
+                d[:, a] -= size[a] * np.round(d[:, a] / size[a])
+        r = np.sqrt((d * d).sum(1))
+        sure = js[r < R - band * scene.h]
+        near = set(js[np.abs(r - R) <= band * scene.h].tolist())
+        if not fluid[i]:
+            sure = sure[fluid[sure]]
+        nf, nb = int(counts[k, 0]), int(counts[k, 1])
+        got = ids[k, :nf + nb]
+        assert len(set(got.tolist())) == nf + nb, f"duplicate neighbours of {i}"
+        assert np.all(fluid[got[:nf]]) and not np.any(fluid[got[nf:nf + nb]]), f"list parts of {i}"
+        g = set(got.tolist()) - near
+        assert g == set(sure.tolist()), f"particle {i}: gpu-oracle {sorted(g - set(sure.tolist()))} " \
+                                        f"oracle-gpu {sorted(set(sure.tolist()) - g)}"
+        assert np.all(ids[k, nf + nb:] == 0xFFFFFFFF)
+        total += len(sure)
+    return total

@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_2207_11328_gb300 import scenes
-from tests.gpu_common import rel_check, require_gpu, sim_for
+from tests.gpu_common import compare_neighbor_sets_of, rel_check, require_gpu, sim_for
 
 pytestmark = pytest.mark.gpu
 TOL_RHS = 1e-5
@@ -97,3 +97,29 @@ def test_fullsize_moving_state_sampled(model):
     sim = sim_for(s, **kw)
     assert sim.stats()["error_bits"] == 0
     _check_sample(s, sim, _sample(s.n, 3000, 12))
+
+
+@pytest.mark.parametrize("dp,name", [(4.3e-3, "dam_break_1M_jitter"), (4.3e-3 / 16 ** (1 / 3), "dam_break_16M_jitter")])
+def test_fullsize_disordered_lists_and_forces_sampled(dp, name):
+    # a disordered full-size state: fluid positions jittered by a seeded U(-0.15, 0.15) dp per
+    # component, seeded velocities and densities; the lists of 3000 sampled particles (half of
+    # them fluid next to the walls, where both list parts are used) against the oracle's
+    # sampled search, bit for bit outside the 1e-6 h band, and their forces within P3
+    s = scenes.dam_break(dp=dp, name=name)
+    f = s.ptype == 0
+    pos = s.pos.copy()
+    pos[f] += scenes.seeded_uniform((int(f.sum()), 3), -0.15 * s.dp, 0.15 * s.dp, 31)
+    vel = s.vel.copy()
+    vel[f] = scenes.seeded_normal((int(f.sum()), 3), 0.1, 32).astype(np.float32)
+    delta = (s.delta + scenes.seeded_normal((s.n,), 1e-3, 33)).astype(np.float32)
+    s = dataclasses.replace(s, pos=pos, vel=vel, delta=delta)
+    sim = sim_for(s)
+    assert sim.stats()["error_bits"] == 0
+    rng = np.random.default_rng(34)
+    nearwall = np.nonzero(f & ((pos[:, 0] < 3 * s.dp) | (pos[:, 2] < 3 * s.dp)))[0]
+    sample = np.unique(np.concatenate([rng.choice(s.n, 1500, replace=False),
+                                       rng.choice(nearwall, 1500, replace=False)])).astype(np.int32)
+    counts, ids = sim.download_neighbors_of(sample)
+    pairs = compare_neighbor_sets_of(s, sample, counts, ids)
+    assert np.any(counts[:, 1] > 0) and pairs > 40 * len(sample)
+    _check_sample(s, sim, sample)

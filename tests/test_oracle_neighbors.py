@@ -70,3 +70,16 @@ def test_dam_break_grid_matches_brute_small():
     off_b, idx_b = oracle.neighbors(p, s.pos, brute=True)
     off_g, idx_g = oracle.neighbors(p, s.pos)
     assert np.array_equal(off_b, off_g) and np.array_equal(idx_b, idx_g)
+
+
+@pytest.mark.parametrize("case", ["box", "dam"])
+def test_sampled_neighbour_sets_equal_the_full_search(case):
+    # the sampled search (used at full sizes) returns, for each sampled particle, exactly
+    # the set of the full search, which is pinned to brute force above
+    s = scenes.periodic_box(n_per_axis=10, jitter=0.3, seed=4) if case == "box" else scenes.dam_break(dp=0.04)
+    p = oracle.params(s)
+    off, idx = oracle.neighbors(p, s.pos)
+    sample = np.sort(np.random.default_rng(5).choice(s.n, size=min(300, s.n), replace=False)).astype(np.int32)
+    so, si = oracle.neighbors_sample(p, s.pos, sample)
+    for k, i in enumerate(sample):
+        assert np.array_equal(si[so[k]:so[k + 1]], idx[off[i]:off[i + 1]])
