@@ -274,6 +274,17 @@ __device__ __forceinline__ void reorder_body(
 // part of each neighbour cell and types need no per-candidate test.
 // ---------------------------------------------------------------------
 
+// m with all but its k lowest set bits cleared
+__device__ __forceinline__ uint32_t lowest_set_bits(uint32_t m, uint32_t k) {
+    uint32_t out = 0u;
+    for (uint32_t c = 0; c < k && m; ++c) {
+        const uint32_t b = m & (0u - m);
+        out |= b;
+        m ^= b;
+    }
+    return out;
+}
+
 // The list of particle i; returns its entry count, *nfound = pairs found
 // (more than max_neibs: overflow, the list keeps the first ones).
 __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __restrict__ pos,
@@ -284,6 +295,7 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
                                                    uint32_t* __restrict__ ncount, uint32_t r2lim, uint32_t max_neibs,
                                                    uint32_t stride, uint32_t* nfound_out, DevStatus* st, uint32_t n) {
     constexpr int kGroup = 6;
+    constexpr int kWindow = 5 * kGroup;  // candidates per hit mask (bits 0..29)
     static_assert(kPosPad >= kGroup - 1, "a group reads up to kGroup - 1 entries past the last particle");
     const SceneDev& sc = scenes[pinfo[i]];
     const float4 pi = pos[i];
@@ -293,38 +305,59 @@ __device__ __forceinline__ uint32_t build_particle(uint32_t i, const float4* __r
     uint32_t nfound = 0;
     ListWriter wf = list_fluid_writer(nlist, i, stride);
     ListWriter wb = list_bnd_writer(nlist, i, stride, max_neibs);
-    // candidates [b, e) of one neighbour cell and one type, appended to w in candidate order:
-    // groups of kGroup candidates (independent loads in flight), hits gathered in a bit mask.
-    // A group may read up to kGroup - 1 entries past the range (the next cell's, or the
-    // kPosPad spare entries at the end): masked off.  With room for the whole group the hits
-    // are appended by predicated puts (no loop whose trip count differs between lanes).
+    // candidates [b, e) of one neighbour cell and one type, appended to w in candidate order.
+    // The distance tests run in groups of kGroup candidates (independent loads in flight); the
+    // hits of up to kWindow candidates are gathered in one bit mask, which a loop over its set
+    // bits then appends: a lane spends append work on its own hits only, where an append
+    // predicated per candidate slot costs the whole warp every slot of a group as soon as one
+    // lane hits in it.  A group may read up to kGroup - 1 entries past the range (the next
+    // cell's, or the kPosPad spare entries at the end): masked off.  Past max_neibs entries the
+    // list keeps the first ones in candidate order (the window's mask is cut to the room left).
     auto scan_part = [&](uint32_t b, uint32_t e, ListWriter& w, float bx, float by, float bz, uint32_t code) {
-        for (uint32_t j = b; j < e; j += kGroup) {
-            uint32_t hits = 0;
-            const float4* pg = pos + j;
+        for (uint32_t j0 = b; j0 < e; j0 += kWindow) {
+            uint32_t mask = 0;
 #pragma unroll
-            for (int u = 0; u < kGroup; ++u) {
-                const float4 pj = pg[u];
-                const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
-                const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
-                hits |= (uint32_t)(__float_as_uint(r2) - 1u < r2lim) << u;
-            }
-            const uint32_t rem = e - j;
-            if (rem < (uint32_t)kGroup) hits &= (1u << rem) - 1u;
-            if (!hits) continue;
-            nfound += __popc(hits);
-            const uint32_t e0 = (j << kCodeBits) | code;
-            if (wf.n + wb.n + kGroup <= max_neibs) {
+            for (int g = 0; g < kWindow; g += kGroup) {
+                const uint32_t j = j0 + (uint32_t)g;
+                if (j >= e) break;
+                const float4* pg = pos + j;
+                uint32_t hits = 0;
 #pragma unroll
-                for (int u = 0; u < kGroup; ++u)
-                    if ((hits >> u) & 1u) w.put(e0 + ((uint32_t)u << kCodeBits));
-            } else {
-                while (hits) {
-                    const int u = __ffs(hits) - 1;
-                    hits &= hits - 1u;
-                    if (wf.n + wb.n < max_neibs) w.put(e0 + ((uint32_t)u << kCodeBits));
+                for (int u = 0; u < kGroup; ++u) {
+                    const float4 pj = pg[u];
+                    const float rx = bx - pj.x, ry = by - pj.y, rz = bz - pj.z;
+                    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    // 0 < r2 < R2 as one unsigned compare on the bits (r2 >= +0)
+                    hits |= (uint32_t)(__float_as_uint(r2) - 1u < r2lim) << u;
                 }
+                const uint32_t rem = e - j;
+                if (rem < (uint32_t)kGroup) hits &= (1u << rem) - 1u;
+                mask |= hits << g;
+            }
+            if (!mask) continue;
+            const uint32_t found = (uint32_t)__popc(mask);
+            nfound += found;
+            const uint32_t room = max_neibs - (wf.n + wb.n);
+            if (found > room) mask = lowest_set_bits(mask, room);
+            const uint32_t e0 = (j0 << kCodeBits) | code;
+            // the first hit completes a chunk left open by the previous range; then two hits
+            // per chunk store, an odd last hit left open
+            if (mask && (w.n & 1u)) {
+                const uint32_t u = (uint32_t)__ffs(mask) - 1u;
+                mask &= mask - 1u;
+                w.put(e0 + (u << kCodeBits));
+            }
+            while (mask) {
+                const uint32_t u0 = (uint32_t)__ffs(mask) - 1u;
+                mask &= mask - 1u;
+                const uint32_t a = e0 + (u0 << kCodeBits);
+                if (!mask) {
+                    w.open(a);
+                    break;
+                }
+                const uint32_t u1 = (uint32_t)__ffs(mask) - 1u;
+                mask &= mask - 1u;
+                w.put2(a, e0 + (u1 << kCodeBits));
             }
         }
     };

@@ -66,6 +66,16 @@ struct ListWriter {
             p += step;
         }
     }
+    // with n even: a whole chunk (a, b), or a as the open entry of the next one
+    __device__ __forceinline__ void put2(uint32_t a, uint32_t b) {
+        *p = make_uint2(a, b);
+        p += step;
+        n += 2u;
+    }
+    __device__ __forceinline__ void open(uint32_t a) {
+        buf.y = a;
+        ++n;
+    }
     __device__ __forceinline__ void flush() {
         if (n & 1u) *p = make_uint2(buf.y, kMarker);
     }
