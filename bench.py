@@ -609,34 +609,68 @@ def run_ours(args, world, rank, local):
                            "simulated_time_s": sf1["time"], "mean_neighbours": inter_f / 2 / max(1.0, ps_f),
                            "n_removed": sf1["n_removed"], "clocks": clk_f}
 
-    # end to end through the public API with host buffers (upload, one step, download)
+    # end to end through the public API with host buffers (upload, one step, download), by
+    # --e2e-workers host threads, each with its own context and stream (the first is the
+    # benchmark's), so that one worker's copies run beside another's kernels
     if args.e2e_steps > 0:
+        import threading
+        from paper_2207_11328_gb300 import build_variant_names, forces_variant_names
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()  # noqa: E731
         hp = {k: pin(v) for k, v in dict(pos=scene.pos, vel=scene.vel, delta=scene.delta.astype(np.float32),
                                           mass=scene.mass, ptype=scene.ptype).items()}
-        out = {"pos": pin(np.empty_like(scene.pos)), "vel": pin(np.empty_like(scene.vel)),
-               "delta": pin(np.empty(scene.n, np.float32))}
+        nw = max(1, args.e2e_workers)
+        workers = [(sim, stream)]
+        for _ in range(nw - 1):
+            s_k = torch.cuda.Stream()
+            sim_k = Simulation.from_scene(scene, max_neibs=args.max_neibs, stream=s_k,
+                                          rebuild_every=args.rebuild_every, skin=args.skin * scene.h)
+            sim_k.set_variants(build=build_variant_names().index(tuned["build"]))
+            sim_k.set_forces_variants(forces_variant_names().index(tuned["forces_predict"]),
+                                      forces_variant_names().index(tuned["forces_correct"]))
+            sim_k.set_fused_predict(bool(sim.step_options()["fused_predict"]))
+            workers.append((sim_k, s_k))
+        outs = [{"pos": pin(np.empty_like(scene.pos)), "vel": pin(np.empty_like(scene.vel)),
+                 "delta": pin(np.empty(scene.n, np.float32))} for _ in workers]
         h2d = sum(v.nbytes for v in hp.values())
-        d2h = sum(v.nbytes for v in out.values())
-        inter = 0.0
+        d2h = sum(v.nbytes for v in outs[0].values())
+        counts = [0.0] * nw
+
+        def e2e_steps(k, nsteps):
+            sim_k, s_k = workers[k]
+            for _ in range(nsteps):
+                sim_k.upload(pos=hp["pos"], vel=hp["vel"], delta=hp["delta"], mass=hp["mass"],
+                             ptype=hp["ptype"], stream=s_k)
+                sim_k.step(1, stream=s_k)
+                sim_k.download(stream=s_k, out=(outs[k]["pos"], outs[k]["vel"], outs[k]["delta"]))
+                # the upload resets the counters: the list entries of its build (the list the
+                # step uses), or the pairs the step's first pass found within 2h (skin list)
+                counts[k] += 2.0 * sim_k.stats(stream=s_k, check=False)[
+                    "interactions" if skin_mode else "list_entries"]
+
+        for k in range(1, nw):   # each extra context's first step (graph capture) outside the timing
+            e2e_steps(k, 1)
+        counts = [0.0] * nw
+        share = [args.e2e_steps // nw + (1 if k < args.e2e_steps % nw else 0) for k in range(nw)]
         torch.cuda.synchronize()
         barrier(world)
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            sim.upload(pos=hp["pos"], vel=hp["vel"], delta=hp["delta"], mass=hp["mass"], ptype=hp["ptype"],
-                       stream=stream)
-            sim.step(1, stream=stream)
-            sim.download(stream=stream, out=(out["pos"], out["vel"], out["delta"]))
-            # the upload resets the counters: the list entries of its build (the list the
-            # step uses), or the pairs the step's first pass found within 2h (skin list)
-            inter += 2.0 * sim.stats(stream=stream, check=False)["interactions" if skin_mode else "list_entries"]
+        threads = [threading.Thread(target=e2e_steps, args=(k, share[k])) for k in range(nw)]
+        for th in threads:
+            th.start()
+        for th in threads:
+            th.join()
         torch.cuda.synchronize()
         t_e2e = allmax(world, time.perf_counter() - t0)
-        line["e2e"] = {"value": allsum(world, inter) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+        line["e2e"] = {"value": allsum(world, sum(counts)) / t_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": args.e2e_steps, "workers": nw,
+                       "ms_per_step": 1e3 * t_e2e / args.e2e_steps,
                        "note": "per step: sph_upload from pinned host arrays (incl. its sort and neighbour "
                                "build), sph_step(1) (dt0 forces pass doubling as the predictor's, "
-                               "corrector), sph_download to pinned host arrays"}
+                               "corrector), sph_download to pinned host arrays and the counters read back; "
+                               "the steps shared by `workers` host threads, each with its own context and "
+                               "stream"}
+        for sim_k, _ in workers[1:]:
+            sim_k.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(scene, args.workload)
     if rank == 0:
@@ -746,26 +780,30 @@ def run_adjoint(args):
     xbar = torch.randn((s.n, 3), device="cuda", dtype=torch.float32)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     times = []
-    for rep in range(args.warmup + 3):
-        sim.upload(s, stream=stream)
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        sim.record(64, 8, stream=stream)
-        ev[1].record(stream)
-        sim.backward(xbar_T=xbar, stream=stream)
-        ev[2].record(stream)
-        sim.upload(s, stream=stream)
-        sim.step(64, stream=stream)
-        ev[3].record(stream)
-        torch.cuda.synchronize()
-        if rep >= args.warmup:
-            times.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+    with ClockSampler(0) as clk:   # clocks sampled over the measured repetitions
+        for rep in range(args.warmup + 3):
+            sim.upload(s, stream=stream)
+            torch.cuda.synchronize()
+            if rep == args.warmup:
+                clk.mark(True)
+            ev[0].record(stream)
+            sim.record(64, 8, stream=stream)
+            ev[1].record(stream)
+            sim.backward(xbar_T=xbar, stream=stream)
+            ev[2].record(stream)
+            sim.upload(s, stream=stream)
+            sim.step(64, stream=stream)
+            ev[3].record(stream)
+            torch.cuda.synchronize()
+            if rep >= args.warmup:
+                times.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]), ev[2].elapsed_time(ev[3])])
+        clk.mark(False)
     t = np.median(np.array(times), axis=0)
     line = {"metric": "forward+backward time, 32^3 periodic box, T=64, checkpoint every 8", "value": t[0] + t[1],
             "unit": "ms", "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "periodic_box_32768, T=64, K=8, dt frozen 3.9e-4 s"},
             "record_ms": t[0], "backward_ms": t[1], "plain_forward_64_steps_ms_incl_upload": t[2],
-            "backward_over_forward": t[1] / t[0]}
+            "backward_over_forward": t[1] / t[0], "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -784,6 +822,8 @@ def main():
     ap.add_argument("--variants", default="",
                     help="build,predictor,corrector variant indices (0..4) instead of autotuning")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-workers", type=int, default=2,
+                    help="host threads (one context and stream each) sharing the end-to-end steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rebuild-every", type=int, default=1,
                     help="neighbour pipeline every k steps with a skin (paper default: 10)")

@@ -230,9 +230,12 @@ __device__ __forceinline__ PairGrad2 pair_grad2(const PairIn2& p, const Phys& ph
 // entries q = l (mod LANES), and the partial sums are combined by a fixed xor
 // tree of shuffles, so the result is deterministic (for a given LANES).  More
 // lanes per particle keep small states (the differentiable run's 32^3 box) from
-// leaving most of the GPU idle.
+// leaving most of the GPU idle.  Seven resident blocks per SM (<= 72 registers, no
+// spills) hold the 4096 warps of that box's four-lane launch in one wave on 152
+// SMs; at the 90 registers the kernel takes uncapped, five blocks fit and a second,
+// one-third-full wave followed (backward 11.5 -> 9.9 ms, measured).
 template <int VISC, bool STAR, int LANES>
-__global__ void __launch_bounds__(kBlock, 2) k_adj_vjp(
+__global__ void __launch_bounds__(kBlock, 7) k_adj_vjp(
     const float4* __restrict__ pos, const float4* __restrict__ vel, const float* __restrict__ phat,
     const float* __restrict__ dphat, const float4* __restrict__ seed, const uint32_t* __restrict__ pinfo,
     const uint32_t* __restrict__ nlist, const uint32_t* __restrict__ ncount, const SceneDev* __restrict__ scenes,
