@@ -405,10 +405,11 @@ def cpu_baseline(scene, workload, target_n=600_000):
     inter, psteps, t = time_oracle_steps(sub, 1)
     where = f"the corner cube x, y, z < {w:.4f} m" if w is not None else "all particles"
     cores = max(1, os.cpu_count() or 1)
-    pinter, pt = time_oracle_parallel(sub, cores)
+    passes = 6   # ~1 s on 16 cores: 10-20 s of CPU work with the single-thread step
+    pinter, pt = time_oracle_parallel(sub, cores, passes)
     return {"value": pinter / pt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"2 force passes of the FP64 oracle on the {sub.n} particles of the workload in {where}, "
-                      f"split over {cores} worker processes ({pinter} interactions, {pt:.1f} s)",
+            "sample": f"{passes} force passes of the FP64 oracle on the {sub.n} particles of the workload in "
+                      f"{where}, split over {cores} worker processes ({pinter} interactions, {pt:.1f} s)",
             "single_thread": {"value": inter / t, "unit": UNIT, "cores": 1, "particle_steps_per_s": psteps / t,
                               "sample": f"1 predictor-corrector step (neighbour search + 2 force passes + dt) "
                                         f"of the same oracle, one thread, same particles ({inter} interactions, "
