@@ -822,7 +822,7 @@ def main():
                          "(0: skip)")
     ap.add_argument("--variants", default="",
                     help="build,predictor,corrector variant indices (0..4) instead of autotuning")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=40)
     ap.add_argument("--e2e-workers", type=int, default=2,
                     help="host threads (one context and stream each) sharing the end-to-end steps")
     ap.add_argument("--no-cpu-baseline", action="store_true")
