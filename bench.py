@@ -620,7 +620,7 @@ def run_ours(args, world, rank, local):
         hp = {k: pin(v) for k, v in dict(pos=scene.pos, vel=scene.vel, delta=scene.delta.astype(np.float32),
                                           mass=scene.mass, ptype=scene.ptype).items()}
         nw = max(1, args.e2e_workers)
-        workers = [(sim, stream)]
+        workers = [(sim, torch.cuda.Stream())]   # every worker on a stream of its own
         for _ in range(nw - 1):
             s_k = torch.cuda.Stream()
             sim_k = Simulation.from_scene(scene, max_neibs=args.max_neibs, stream=s_k,
@@ -648,7 +648,8 @@ def run_ours(args, world, rank, local):
                 counts[k] += 2.0 * sim_k.stats(stream=s_k, check=False)[
                     "interactions" if skin_mode else "list_entries"]
 
-        for k in range(1, nw):   # each extra context's first step (graph capture) outside the timing
+        torch.cuda.synchronize()
+        for k in range(nw):   # each worker's first step (graph capture on its stream) outside the timing
             e2e_steps(k, 1)
         counts = [0.0] * nw
         share = [args.e2e_steps // nw + (1 if k < args.e2e_steps % nw else 0) for k in range(nw)]

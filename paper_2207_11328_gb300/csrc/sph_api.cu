@@ -43,6 +43,7 @@ struct sph_ctx {
     Geometry g{};
     Buffers b{};
     std::vector<SceneDev> scenes_h;
+    std::vector<double> centres_h;   // FP64 cell centres (Buffers::centres), per scene and axis
     int cur = 0;
     int device = 0;
     uint32_t n_uploaded = 0;
@@ -115,10 +116,49 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // Upload: FP64 absolute position -> (cell, FP32 offset from the cell
 // centre) per scene grid; type packed in the sign of pos.w.
 // ---------------------------------------------------------------------
+// x truncated to FP32 with integer operations on its bits (no FP64 instruction): sign,
+// exponent re-biased, the top 23 fraction bits; magnitudes below FP32's normal range give
+// +-0, above it +-FLT_MAX.  Only the upload's cell estimate uses it.
+__device__ __forceinline__ float fp32_estimate(double x) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int e = (int)((hi >> 20) & 0x7ffu) - 1023 + 127;
+    const uint32_t sign = hi & 0x80000000u;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f7fffffu);
+    return __uint_as_float(sign | ((uint32_t)e << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+}
+
+// d rounded to FP32 (to nearest, ties to even) with integer operations on its bits: the
+// same result as the FP64 unit's conversion over FP32's normal range; magnitudes below it
+// give +-0 (cell offsets that small are below any resolution the state carries).
+__device__ __forceinline__ float fp32_rn(double d) {
+    const uint64_t b = (uint64_t)__double_as_longlong(d);
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7ffu) - 1023 + 127;
+    if (e <= 0) return __uint_as_float(sign);
+    if (e >= 255) return __uint_as_float(sign | 0x7f800000u);
+    const uint64_t m = b & 0xfffffffffffffull;
+    const uint32_t f = (uint32_t)(m >> 29), rest = (uint32_t)(m & 0x1fffffffu);
+    uint32_t bits = sign | ((uint32_t)e << 23) | f;
+    if (rest > 0x10000000u || (rest == 0x10000000u && (f & 1u))) bits += 1u;  // a carry moves to the next binade
+    return __uint_as_float(bits);
+}
+
+// f widened to FP64 exactly with integer operations (FP32 subnormals, never a cell offset
+// of the state at any resolution used, give +-0)
+__device__ __forceinline__ double fp64_of(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t e = (b >> 23) & 0xffu;
+    const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+    if (e == 0u) return __longlong_as_double((long long)sign);
+    return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127u + 1023u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
+}
+
 __global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float* __restrict__ vel,
                          const float* __restrict__ delta, const float* __restrict__ mass,
                          const uint8_t* __restrict__ type, const uint32_t* __restrict__ scene,
-                         const SceneDev* __restrict__ scenes, uint32_t n_scenes, float4* __restrict__ pos_o,
+                         const SceneDev* __restrict__ scenes, const double* __restrict__ centres,
+                         uint32_t n_scenes, float4* __restrict__ pos_o,
                          float4* __restrict__ vel_o, float* __restrict__ phat_o, uint32_t* __restrict__ cell_o,
                          uint32_t* __restrict__ pinfo_o, uint32_t* __restrict__ pid_o, DevStatus* __restrict__ st,
                          const Phys ph) {
@@ -133,23 +173,45 @@ __global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float
         float o[3];
         for (int a = 0; a < 3; ++a) {
             double x = pos[3 * i + a];
-            if (!isfinite(x)) {
+            // The FP64 units are slow on this GPU, so the FP64 work is one subtraction per
+            // axis: the finiteness test reads the exponent bits, the cell is estimated from
+            // an FP32 copy of x built from its bits (truncated: relative error < 2^-23, so the
+            // estimate can be off by one within ~1e-7 of a cell face), the offset from that
+            // cell's FP64 centre (exact where x and the centre are within a factor of two of
+            // each other, i.e. away from the cells at the coordinate origin; else rounded once
+            // in FP64) is rounded to FP32 by integer operations.  A particle that lands a hair past a face is
+            // re-based into the next cell by the sort that follows.  Only the outer cells take
+            // the exact FP64 domain test; a periodic axis is wrapped in FP64 first.
+            if ((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) {
                 bad |= kUpNonFinite;
                 x = sc.origin[a];
             }
-            double L = sc.cell_d[a] * sc.ncell[a];
-            double rel = x - sc.origin[a];
-            if ((sc.periodic >> a) & 1u) rel -= L * floor(rel / L);
-            int k = (int)floor(rel / sc.cell_d[a]);
-            if ((sc.periodic >> a) & 1u) {
-                if (k >= sc.ncell[a]) k = sc.ncell[a] - 1;
-                if (k < 0) k = 0;
-            } else if (k < 0 || k >= sc.ncell[a]) {
-                bad |= kUpOutOfDomain;
-                k = 0;
+            const bool per = (sc.periodic >> a) & 1u;
+            if (per) {
+                const double L = sc.cell_d[a] * sc.ncell[a];
+                const double rel = x - sc.origin[a];
+                x = sc.origin[a] + (rel - L * floor(rel * sc.inv_len_d[a]));
             }
+            const float xe = fp32_estimate(x);
+            const float relf = xe - sc.origin_f[a];
+            int k = (int)floorf(relf * sc.inv_cell_f[a]);
+            // outer cells: the FP32 estimate decides unless it lies within a margin of a face
+            // that covers its own errors (truncation, the rounded origin and length, the
+            // subtraction: each below 2.5e-7 of the magnitudes involved), then FP64 decides
+            const float lenf = sc.cell_f[a] * (float)sc.ncell[a];
+            const float tol = 1e-6f * (fabsf(xe) + fabsf(sc.origin_f[a]) + lenf);
+            if (!per && (k <= 0 || k >= sc.ncell[a] - 1) && !(relf >= tol && relf <= lenf - tol)) {
+                const double L = sc.cell_d[a] * sc.ncell[a];
+                const double rel = x - sc.origin[a];
+                if (!(rel >= 0.0 && rel < L)) {
+                    bad |= kUpOutOfDomain;
+                    x = sc.origin[a];
+                    k = 0;
+                }
+            }
+            k = min(max(k, 0), sc.ncell[a] - 1);
             c[a] = k;
-            o[a] = (float)(rel - (k + 0.5) * sc.cell_d[a]);
+            o[a] = fp32_rn(x - centres[sc.centre_off[a] + (uint32_t)k]);
         }
         const bool fluid = t == 0;
         float4 v = make_float4(0.f, 0.f, 0.f, delta[i]);
@@ -197,7 +259,7 @@ __device__ __forceinline__ double wrap_periodic(double x, const SceneDev& sc, in
     if ((sc.periodic >> a) & 1u) {
         const double L = sc.cell_d[a] * sc.ncell[a];
         const double rel = x - sc.origin[a];
-        x = sc.origin[a] + (rel - L * floor(rel / L));
+        x = sc.origin[a] + (rel - L * floor(rel * sc.inv_len_d[a]));
     }
     return x;
 }
@@ -205,6 +267,7 @@ __device__ __forceinline__ double wrap_periodic(double x, const SceneDev& sc, in
 __global__ void k_download(const float4* __restrict__ pos, const float4* __restrict__ vel,
                            const uint32_t* __restrict__ cell, const uint32_t* __restrict__ pinfo,
                            const uint32_t* __restrict__ pid, const SceneDev* __restrict__ scenes,
+                           const double* __restrict__ centres,
                            const DevStatus* __restrict__ st, uint32_t n_up, double* __restrict__ pos_o,
                            float* __restrict__ vel_o, float* __restrict__ delta_o) {
     const uint32_t n = st->n_active;
@@ -219,7 +282,7 @@ __global__ void k_download(const float4* __restrict__ pos, const float4* __restr
         const float o[3] = {p.x, p.y, p.z};
         if (pos_o)
             for (int a = 0; a < 3; ++a)
-                pos_o[3 * (size_t)id + a] = wrap_periodic(sc.origin[a] + (c[a] + 0.5) * sc.cell_d[a] + (double)o[a], sc, a);
+                pos_o[3 * (size_t)id + a] = wrap_periodic(centres[sc.centre_off[a] + (uint32_t)c[a]] + fp64_of(o[a]), sc, a);
         if (vel_o) {
             vel_o[3 * (size_t)id] = v.x;
             vel_o[3 * (size_t)id + 1] = v.y;
@@ -305,6 +368,8 @@ int scene_from(const sph_params& p, const double origin[3], const double size[3]
         s.ncell[a] = (int32_t)k;
         s.origin[a] = origin[a];
         s.cell_d[a] = size[a] / k;
+        s.inv_len_d[a] = 1.0 / (s.cell_d[a] * k);
+        s.origin_f[a] = (float)origin[a];
         s.cell_f[a] = (float)s.cell_d[a];
         s.inv_cell_f[a] = (float)(1.0 / s.cell_d[a]);
         ncells *= (uint64_t)k;
@@ -337,9 +402,11 @@ void free_cells(sph_ctx* c) {
     cudaFree(c->b.cell_nfluid);
     cudaFree(c->b.scenes);
     cudaFree(c->b.dyn);
+    cudaFree(c->b.centres);
     c->b.count = c->b.start = c->b.bsum = c->b.cell_nfluid = nullptr;
     c->b.scenes = nullptr;
     c->b.dyn = nullptr;
+    c->b.centres = nullptr;
 }
 
 void drop_graphs(sph_ctx* c) {
@@ -365,6 +432,8 @@ int alloc_cells(sph_ctx* c) {
     CK(cudaMemcpy(c->b.scenes, c->scenes_h.data(), sizeof(SceneDev) * c->g.n_scenes, cudaMemcpyHostToDevice));
     CK(cudaMalloc(&c->b.dyn, sizeof(SceneDyn) * c->g.n_scenes));
     CK(cudaMemset(c->b.dyn, 0, sizeof(SceneDyn) * c->g.n_scenes));
+    CK(cudaMalloc(&c->b.centres, sizeof(double) * c->centres_h.size()));
+    CK(cudaMemcpy(c->b.centres, c->centres_h.data(), sizeof(double) * c->centres_h.size(), cudaMemcpyHostToDevice));
     return SPH_OK;
 }
 
@@ -378,9 +447,19 @@ int set_scene_table(sph_ctx* c, uint32_t n, const sph_scene* sc) {
         off += nc;
         if (off >= 0xF0000000ull) return SPH_ERR_ARG;
     }
+    // FP64 cell centres, origin + (k + 1/2) cell per axis and scene (upload and download
+    // convert between absolute positions and cell + offset with them)
+    std::vector<double> centres;
+    for (uint32_t s = 0; s < n; ++s)
+        for (int a = 0; a < 3; ++a) {
+            tab[s].centre_off[a] = (uint32_t)centres.size();
+            for (int k = 0; k < tab[s].ncell[a]; ++k) centres.push_back(tab[s].origin[a] + (k + 0.5) * tab[s].cell_d[a]);
+        }
+    if (centres.size() >= 0xFFFFFFFFull) return SPH_ERR_ARG;
     drop_graphs(c);
     free_cells(c);
     c->scenes_h = tab;
+    c->centres_h = centres;
     c->g.n_scenes = n;
     c->g.n_cells = (uint32_t)off;
     c->ph.n_scenes = n;
@@ -482,7 +561,8 @@ int do_upload(sph_ctx* c, uint32_t n, const double* pos, const float* vel, const
     k_set_status_n<<<1, 1, 0, st>>>(c->b.status, n);
     k_reset_dyn<<<1, 256, 0, st>>>(c->b.dyn, c->g.n_scenes);
     if (n) {
-        k_upload<<<grid_for(n, 256), 256, 0, st>>>(n, pos, vel, delta, mass, type, scene, c->b.scenes, c->g.n_scenes,
+        k_upload<<<grid_for(n, 256), 256, 0, st>>>(n, pos, vel, delta, mass, type, scene, c->b.scenes, c->b.centres,
+                                                    c->g.n_scenes,
                                                     c->b.pos[c->cur], c->b.vel[c->cur], c->b.phat[c->cur],
                                                     c->b.cell[c->cur], c->b.pinfo[c->cur], c->b.pid[c->cur],
                                                     c->b.status, c->ph);
@@ -1393,6 +1473,7 @@ int sph_download_device(sph_ctx* c, uint32_t n, double* pos, float* vel, float* 
         if (delta) CK(cudaMemsetAsync(delta, 0xFF, sizeof(float) * n, st));
         k_download<<<grid_for(c->g.cap, 256), 256, 0, st>>>(c->b.pos[c->cur], c->b.vel[c->cur], c->b.cell[c->cur],
                                                              c->b.pinfo[c->cur], c->b.pid[c->cur], c->b.scenes,
+                                                             c->b.centres,
                                                              c->b.status, n, pos, vel, delta);
         CK(cudaGetLastError());
     }

@@ -93,6 +93,9 @@ __device__ __forceinline__ ListWriter list_bnd_writer(uint32_t* nlist, uint32_t 
 struct SceneDev {
     double origin[3];
     double cell_d[3];        // cell side in FP64 (upload/download conversion)
+    double inv_len_d[3];     // 1 / (cell_d * ncell): the periodic wrap by a product
+    uint32_t centre_off[3];  // this scene's cell centres per axis in Buffers::centres
+    float origin_f[3];       // origin in FP32 (the upload's cell estimate)
     float cell_f[3];         // cell side in FP32 (device geometry)
     float inv_cell_f[3];
     int32_t ncell[3];
@@ -266,6 +269,7 @@ struct Buffers {
     uint32_t* ncount;
     SceneDev* scenes;
     SceneDyn* dyn;
+    double* centres;         // FP64 cell centres origin + (k + 1/2) cell, per scene and axis
     DevStatus* status;
     void* staging;           // upload/download staging (64 B per particle)
 };

@@ -59,6 +59,29 @@ def test_out_of_domain_upload_rejected():
     assert e.value.code == -5
 
 
+@pytest.mark.parametrize("axis", [0, 1, 2])
+def test_domain_faces_decided_exactly(axis):
+    # positions on and next to the faces of the domain [origin, origin + size) of a non-periodic
+    # axis: inside the FP32 estimate's margin of a face (1e-6 of the magnitudes) the upload
+    # decides in FP64.  (A particle within FP32 resolution below the upper face is re-based
+    # out of the domain by the first sort, so the inside case there keeps 1e-6 of the size.)
+    base = scenes.dam_break(dp=0.05)
+    lo, size = base.origin[axis], base.size[axis]
+    cases = [(lo, True), (np.nextafter(lo, -np.inf), False), (lo + 1e-9 * size, True), (lo - 1e-9 * size, False),
+             (lo + size - 1e-6 * size, True), (lo + size + 1e-9 * size, False), (lo + 0.5 * size, True)]
+    for x, inside in cases:
+        s = scenes.dam_break(dp=0.05)
+        s.pos = s.pos.copy()
+        s.pos[0, axis] = x
+        if inside:
+            sim = sim_for(s)
+            assert sim.stats()["n_active"] == s.n
+        else:
+            with pytest.raises(SphError) as e:
+                sim_for(s)
+            assert e.value.code == -5
+
+
 def test_nonfinite_upload_rejected():
     s = scenes.periodic_box(n_per_axis=8)
     s.vel = s.vel.copy()
