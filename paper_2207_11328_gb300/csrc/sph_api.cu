@@ -154,6 +154,59 @@ __device__ __forceinline__ double fp64_of(float f) {
     return __longlong_as_double((long long)(sign | ((uint64_t)(e - 127u + 1023u) << 52) | ((uint64_t)(b & 0x7fffffu) << 29)));
 }
 
+// x - c rounded once to FP32 (to nearest, ties to even) with integer operations, when x and c
+// have the same sign and exponents at most one apart: their significands then align within 54
+// bits and the difference is exact before the rounding.  Returns false otherwise (the caller
+// subtracts in FP64).  Results below FP32's normal range give +-0, as fp32_rn.
+__device__ __forceinline__ bool sub_to_fp32(double x, double c, float* out) {
+    const uint64_t bx = (uint64_t)__double_as_longlong(x), bc = (uint64_t)__double_as_longlong(c);
+    const uint32_t ex = (uint32_t)(bx >> 52) & 0x7ffu, ec = (uint32_t)(bc >> 52) & 0x7ffu;
+    if (((bx ^ bc) >> 63) != 0u || ex == 0u || ec == 0u || ex == 0x7ffu || ec == 0x7ffu || ex > ec + 1u ||
+        ec > ex + 1u)
+        return false;
+    const uint64_t frac = (1ull << 52) - 1ull;
+    const uint32_t e0 = min(ex, ec);
+    const int64_t d = (int64_t)(((1ull << 52) | (bx & frac)) << (ex - e0)) -
+                      (int64_t)(((1ull << 52) | (bc & frac)) << (ec - e0));
+    if (d == 0) {
+        *out = 0.f;
+        return true;
+    }
+    const uint32_t sign = ((uint32_t)(bx >> 32) ^ (d < 0 ? 0x80000000u : 0u)) & 0x80000000u;
+    const uint64_t m = d < 0 ? (uint64_t)(-d) : (uint64_t)d;
+    const int top = 63 - __clzll((long long)m);            // the leading bit of |d|
+    const int e32 = (int)e0 - 1023 - 52 + top + 127;       // biased FP32 exponent
+    if (e32 <= 0) {
+        *out = __uint_as_float(sign);
+        return true;
+    }
+    uint32_t b;
+    if (top >= 24) {
+        const int sh = top - 23;
+        const uint32_t f = (uint32_t)(m >> sh) & 0x7fffffu;
+        const uint64_t rest = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+        b = sign | ((uint32_t)e32 << 23) | f;
+        if (rest > half || (rest == half && (f & 1u))) b += 1u;   // a carry moves to the next binade
+    } else {
+        b = sign | ((uint32_t)e32 << 23) | ((uint32_t)(m << (23 - top)) & 0x7fffffu);
+    }
+    *out = __uint_as_float(b);
+    return true;
+}
+
+// The upload's rare FP64 paths, kept out of line so that they stay branches taken by the few
+// particles that need them rather than instructions every particle executes under a predicate.
+__device__ __noinline__ double wrap_into_domain(double x, const SceneDev& sc, int a) {
+    const double L = sc.cell_d[a] * sc.ncell[a];
+    const double rel = x - sc.origin[a];
+    return sc.origin[a] + (rel - L * floor(rel * sc.inv_len_d[a]));
+}
+__device__ __noinline__ bool inside_domain(double x, const SceneDev& sc, int a) {
+    const double rel = x - sc.origin[a];
+    return rel >= 0.0 && rel < sc.cell_d[a] * sc.ncell[a];
+}
+__device__ __noinline__ float offset_fp64(double x, double centre) { return fp32_rn(x - centre); }
+
 __global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float* __restrict__ vel,
                          const float* __restrict__ delta, const float* __restrict__ mass,
                          const uint8_t* __restrict__ type, const uint32_t* __restrict__ scene,
@@ -173,25 +226,21 @@ __global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float
         float o[3];
         for (int a = 0; a < 3; ++a) {
             double x = pos[3 * i + a];
-            // The FP64 units are slow on this GPU, so the FP64 work is one subtraction per
-            // axis: the finiteness test reads the exponent bits, the cell is estimated from
-            // an FP32 copy of x built from its bits (truncated: relative error < 2^-23, so the
-            // estimate can be off by one within ~1e-7 of a cell face), the offset from that
-            // cell's FP64 centre (exact where x and the centre are within a factor of two of
-            // each other, i.e. away from the cells at the coordinate origin; else rounded once
-            // in FP64) is rounded to FP32 by integer operations.  A particle that lands a hair past a face is
-            // re-based into the next cell by the sort that follows.  Only the outer cells take
-            // the exact FP64 domain test; a periodic axis is wrapped in FP64 first.
+            // The FP64 units are slow on this GPU, so the common path has no FP64 instruction:
+            // the finiteness test reads the exponent bits, the cell is estimated from an FP32
+            // copy of x built from its bits (truncated: relative error < 2^-23, so the estimate
+            // can be off by one within ~1e-7 of a cell face), and the offset from that cell's
+            // FP64 centre is the exact difference rounded once to FP32, by integer operations
+            // (sub_to_fp32; an FP64 subtraction only near the coordinate origin, where x and the
+            // centre can differ in sign or binade).  A particle that lands a hair past a face is
+            // re-based into the next cell by the sort that follows.  Within 1e-6 of a face of
+            // the domain the domain test runs in FP64; a periodic axis is wrapped in FP64 first.
             if ((__double2hiint(x) & 0x7ff00000) == 0x7ff00000) {
                 bad |= kUpNonFinite;
                 x = sc.origin[a];
             }
             const bool per = (sc.periodic >> a) & 1u;
-            if (per) {
-                const double L = sc.cell_d[a] * sc.ncell[a];
-                const double rel = x - sc.origin[a];
-                x = sc.origin[a] + (rel - L * floor(rel * sc.inv_len_d[a]));
-            }
+            if (per) x = wrap_into_domain(x, sc, a);
             const float xe = fp32_estimate(x);
             const float relf = xe - sc.origin_f[a];
             int k = (int)floorf(relf * sc.inv_cell_f[a]);
@@ -200,18 +249,16 @@ __global__ void k_upload(uint32_t n, const double* __restrict__ pos, const float
             // subtraction: each below 2.5e-7 of the magnitudes involved), then FP64 decides
             const float lenf = sc.cell_f[a] * (float)sc.ncell[a];
             const float tol = 1e-6f * (fabsf(xe) + fabsf(sc.origin_f[a]) + lenf);
-            if (!per && (k <= 0 || k >= sc.ncell[a] - 1) && !(relf >= tol && relf <= lenf - tol)) {
-                const double L = sc.cell_d[a] * sc.ncell[a];
-                const double rel = x - sc.origin[a];
-                if (!(rel >= 0.0 && rel < L)) {
-                    bad |= kUpOutOfDomain;
-                    x = sc.origin[a];
-                    k = 0;
-                }
+            if (!per && (k <= 0 || k >= sc.ncell[a] - 1) && !(relf >= tol && relf <= lenf - tol) &&
+                !inside_domain(x, sc, a)) {
+                bad |= kUpOutOfDomain;
+                x = sc.origin[a];
+                k = 0;
             }
             k = min(max(k, 0), sc.ncell[a] - 1);
             c[a] = k;
-            o[a] = fp32_rn(x - centres[sc.centre_off[a] + (uint32_t)k]);
+            const double centre = centres[sc.centre_off[a] + (uint32_t)k];
+            if (!sub_to_fp32(x, centre, &o[a])) o[a] = offset_fp64(x, centre);
         }
         const bool fluid = t == 0;
         float4 v = make_float4(0.f, 0.f, 0.f, delta[i]);
