@@ -302,13 +302,9 @@ __global__ void k_reset_dyn(SceneDyn* dyn, uint32_t n_scenes) {
     }
 }
 
+// the download's periodic wrap: a branch for periodic axes only (out of line, as in the upload)
 __device__ __forceinline__ double wrap_periodic(double x, const SceneDev& sc, int a) {
-    if ((sc.periodic >> a) & 1u) {
-        const double L = sc.cell_d[a] * sc.ncell[a];
-        const double rel = x - sc.origin[a];
-        x = sc.origin[a] + (rel - L * floor(rel * sc.inv_len_d[a]));
-    }
-    return x;
+    return ((sc.periodic >> a) & 1u) ? wrap_into_domain(x, sc, a) : x;
 }
 
 __global__ void k_download(const float4* __restrict__ pos, const float4* __restrict__ vel,
