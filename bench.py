@@ -589,7 +589,8 @@ def run_ours(args, world, rank, local):
                                   f"every {args.rebuild_every} steps, list radius 2h + {args.skin}h",
                        "state": f"initial column at rest after {args.warmup} warm-up steps",
                        "l2": "inputs larger than L2 (no flush)", "parallelism": f"replicas x{world}",
-                       "variants": dict(tuned, autotuned=not args.variants)},
+                       "variants": dict(tuned, autotuned=not args.variants,
+                                        fused_build_predict=bool(sim.step_options()["fused_predict"]))},
             "particle_steps_per_s": psteps, "mean_neighbours": inter_local / 2 / max(1.0, psteps_local),
             "list_builds": st1["builds"] - st0["builds"],
             "roofline": roofline, "gpu_launches": int(kernels * args.steps),
@@ -753,7 +754,8 @@ def run_batch(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"sloshing_batch: {len(b.scenes)} tanks, {b.n} particles "
                                    f"({b.n_fluid} fluid), dp 0.01 m",
-                                   "variants": dict(tuned, autotuned=True)},
+                                   "variants": dict(tuned, autotuned=True,
+                                                    fused_build_predict=bool(sim.step_options()["fused_predict"]))},
             "particle_steps_per_s": b.n * args.steps / t_b,
             "per_scene_launches": {"value": inter_p / t_p, "ms_per_step": 1e3 * t_p / ps_steps,
                                    "particle_steps_per_s": b.n * ps_steps / t_p, "steps": ps_steps,
