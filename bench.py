@@ -317,23 +317,47 @@ def oracle_window(scene, target_n):
     from paper_2207_11328_gb300 import scenes
     if target_n >= scene.n:
         return scene, None
-    lo, hi = 0.0, float(np.max(scene.pos) + 1.0)
-    for _ in range(60):
-        w = 0.5 * (lo + hi)
-        k = int(np.count_nonzero(np.all(scene.pos < w, axis=1)))
-        lo, hi = (w, hi) if k < target_n else (lo, w)
-    mask = np.all(scene.pos < hi, axis=1)
-    return scenes.subset(scene, mask, name=scene.name + f"_corner{hi:.4f}"), hi
+    # a particle is inside the cube iff its largest coordinate is below w: w just above
+    # the target_n-th smallest of those maxima (one selection pass)
+    top = np.max(scene.pos, axis=1)
+    w = float(np.nextafter(np.partition(top, target_n - 1)[target_n - 1], np.inf))
+    mask = top < w
+    sub = scenes.subset(scene, mask, name=scene.name + f"_corner{w:.4f}")
+    # the sample's own domain on the non-periodic axes: its extent twice over plus two
+    # influence radii (room to move during a run), within the workload's, so that the
+    # oracle bins the sample rather than the whole tank at the workload's resolution
+    import dataclasses
+    origin, size = np.asarray(scene.origin, np.float64), np.asarray(scene.size, np.float64)
+    ext = 2.0 * (w - origin) + 2.0 * scene.kernel_radius * scene.h
+    per = np.array([(scene.periodic >> a) & 1 for a in range(3)], bool)
+    size = np.where(per, size, np.minimum(size, ext))
+    return dataclasses.replace(sub, size=tuple(float(v) for v in size)), w
 
 
 def interactions_of(p, sub, x):
     """Pairs a step evaluates twice: all neighbours of fluid particles, fluid
-    neighbours of boundary particles (boundary-boundary pairs carry nothing)."""
-    import oracle
-    off, idx = oracle.neighbors(p, x)
-    per = np.repeat(np.arange(sub.n), np.diff(off))
-    keep = (sub.ptype[per] == 0) | (sub.ptype[idx] == 0)
-    return int(np.count_nonzero(keep))
+    neighbours of boundary particles (boundary-boundary pairs carry nothing), as
+    ordered pairs at distance 0 < r < 2h.  Bookkeeping for the metric, counted
+    with a k-d tree over the sample (the oracle's own search bins the whole
+    domain of the workload on every call); periodic axes by minimum image."""
+    from scipy.spatial import cKDTree
+    per = np.array([(sub.periodic >> a) & 1 for a in range(3)], bool)
+    R = float(np.nextafter(sub.kernel_radius * sub.h, 0.0))        # r < 2h
+    pts = np.array(x, np.float64) - np.asarray(sub.origin, np.float64)
+    if per.any():
+        size = np.asarray(sub.size, np.float64)
+        pts[:, per] = np.mod(pts[:, per], size[per])
+        pts[:, per] = np.where(pts[:, per] >= size[per], 0.0, pts[:, per])
+        pts[:, ~per] -= pts[:, ~per].min(axis=0)
+        box = np.where(per, size, pts.max(axis=0) + 2.0 * R + 1.0)   # no wrap on the other axes
+        tree = lambda q: cKDTree(q, boxsize=box)  # noqa: E731
+    else:
+        tree = cKDTree
+    b = sub.ptype != 0
+    t_all, t_b = tree(pts), tree(pts[b])
+    n_all = int(t_all.count_neighbors(t_all, R)) - sub.n            # ordered pairs, self-pairs removed
+    n_bb = int(t_b.count_neighbors(t_b, R)) - int(np.count_nonzero(b))
+    return n_all - n_bb
 
 
 def time_oracle_steps(sub, steps, warmup=0):
@@ -420,8 +444,9 @@ def run_reference(args, world, rank):
     if rank != 0:
         return
     scene, wdesc = make_workload(args.workload)
-    # size the sample so the whole --steps/--warmup run stays within a few minutes
-    budget = 150.0 / max(1, args.steps + args.warmup)
+    # size the sample so the whole --steps/--warmup run stays within a few minutes: ~75 s of
+    # timed oracle steps, and about as much again for each step's untimed pair count
+    budget = 75.0 / max(1, args.steps + args.warmup)
     probe, _ = oracle_window(scene, 20_000)
     _, pn, pt = time_oracle_steps(probe, 1)
     rate = pn / max(pt, 1e-9)                     # particle-steps/s of the oracle
