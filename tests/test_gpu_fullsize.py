@@ -75,7 +75,7 @@ def test_fullsize_one_step_sampled():
 def _dam_moving(dp=4.3e-3):
     # the benchmark's dam break with a seeded velocity field and density perturbation,
     # so that the continuity sum, the switched viscosity and the diffusion are all active
-    s = scenes.dam_break(dp=dp, name="dam_break_1M_moving")
+    s = scenes.dam_break(dp=dp, name="dam_break_1M_moving" if dp >= 4e-3 else "dam_break_16M_moving")
     f = s.ptype == 0
     vel = s.vel.copy()
     vel[f] = scenes.seeded_normal((int(f.sum()), 3), 0.2, 23).astype(np.float32)
@@ -83,16 +83,16 @@ def _dam_moving(dp=4.3e-3):
     return dataclasses.replace(s, vel=vel, delta=delta.astype(np.float32))
 
 
-@pytest.mark.parametrize("model", ["default", "density_diffusion", "all_options", "skin_list"])
+@pytest.mark.parametrize("model", ["default", "density_diffusion", "all_options", "skin_list", "skin_list_16M"])
 def test_fullsize_moving_state_sampled(model):
-    s = _dam_moving()
+    s = _dam_moving(4.3e-3 / 16 ** (1 / 3)) if model.endswith("16M") else _dam_moving()
     kw = {}
     if model == "density_diffusion":
         s = dataclasses.replace(s, ddiff=1, ddiff_coef=0.1)
     elif model == "all_options":
         s = dataclasses.replace(s, kernel_type=1, formulation=1, visc=3, visc_avg=1, alpha=0.0, nu=1e-6, zeta=1e-6,
                                 ddiff=1, ddiff_coef=0.1)
-    elif model == "skin_list":
+    elif model.startswith("skin_list"):
         kw = dict(rebuild_every=10, skin=0.3 * s.h, max_neibs=192)
     sim = sim_for(s, **kw)
     assert sim.stats()["error_bits"] == 0
