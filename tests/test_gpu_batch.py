@@ -55,6 +55,33 @@ def test_batch_256_tanks_runs():
     assert np.all(dts > 0) and np.all(times > 0)
 
 
+def test_batch_256_tanks_forces_and_dt_match_the_oracle_sampled():
+    # the full batch of 256 tanks (8.6M particles): forces of 200 sampled particles in each
+    # of 12 seeded tanks, and the first time step of the three smallest tanks, against the
+    # oracle run on each tank alone with its own grid and sound speed
+    b = scenes.sloshing_batch()
+    sim = sim_for(b)
+    sim.forces()
+    acc, drho = sim.download_forces()
+    rng = np.random.default_rng(85)
+    for s in rng.choice(len(b.scenes), 12, replace=False):
+        one = _alone(b, int(s))
+        ids = np.nonzero(b.scene == s)[0]
+        sample = np.sort(rng.choice(len(ids), min(200, len(ids)), replace=False)).astype(np.int32)
+        a_ref, d_ref, _, mag = oracle.rhs_sample(oracle.params(one), one.pos, one.vel, one.delta, one.mass,
+                                                 one.ptype, sample)
+        rel_check(acc[ids[sample]], a_ref, 1e-5, f"tank {s} acceleration", mag[:, 0])
+        rel_check(drho[ids[sample]], d_ref, 1e-5, f"tank {s} density rate", mag[:, 1])
+    sim.step(1)
+    dts, _ = sim.scene_times()
+    sizes = np.bincount(b.scene, minlength=len(b.scenes))
+    for s in np.argsort(sizes)[:3]:
+        one = _alone(b, int(s))
+        p = oracle.params(one)
+        a, _ = oracle.rhs(p, one.pos, one.vel, one.delta, one.mass, one.ptype)
+        assert dts[s] == pytest.approx(oracle.cfl_dt(p, a, one.ptype), rel=1e-5)
+
+
 def test_batch_model_options_match_the_oracle_per_scene():
     # per-scene sound speed enters the viscosity and the density diffusion: each tank's
     # forces against the oracle run on that tank alone with its own c0
