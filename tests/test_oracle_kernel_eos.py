@@ -6,6 +6,7 @@ f = (q-2)^3) with the unit-integral and compact-support properties of
 Section 2.1; Cole equation of state of Section 2.1.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -57,6 +58,19 @@ def test_shape_matches_listing():
     for q in (0.1, 0.5, 1.0, 1.5, 1.9):
         assert oracle.kernel_W(q * H, H) / W0 == pytest.approx((2 * q + 1) * (1 - q / 2) ** 4, rel=1e-13)
         assert oracle.kernel_F(q * H, H) / F0 == pytest.approx((q - 2) ** 3 / -8.0, rel=1e-13)
+
+
+def test_shape_matches_the_golden_values():
+    # tests/golden/kernel_shapes.txt: exact values of the printed Wendland polynomials
+    path = os.path.join(os.path.dirname(__file__), "golden", "kernel_shapes.txt")
+    rows = [line.split() for line in open(path) if line.strip() and not line.startswith("#")]
+    assert len(rows) >= 5
+    W0, F0 = oracle.kernel_W(0.0, H), oracle.kernel_F(1e-300, H)
+    w0, f0 = Fraction(rows[0][1]), Fraction(rows[0][2])
+    for q, w, f in rows:
+        q, w, f = Fraction(q), Fraction(w), Fraction(f)
+        assert oracle.kernel_W(float(q) * H, H) / W0 == pytest.approx(float(w / w0), rel=1e-13, abs=1e-15)
+        assert oracle.kernel_F(float(q) * H, H) / F0 == pytest.approx(float(f / f0), rel=1e-13, abs=1e-15)
 
 
 def _exact_pressure(delta, rho0, c0, gamma):
