@@ -82,6 +82,27 @@ __global__ void __launch_bounds__(kPipeBlock) k_reorder(
 // ---------------------------------------------------------------------
 constexpr int kStage = 256;  // staged candidates per warp and window (multiple of 32)
 
+// the entries e[u] of the set bits u of `mask` appended to w in bit order: the first completes
+// a chunk left open, then two entries per 8-byte chunk store, an odd last one left open
+__device__ __forceinline__ void append_hits(ListWriter& w, uint32_t mask, const uint32_t* e) {
+    if (mask && (w.n & 1u)) {
+        const int u = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        w.put(e[u]);
+    }
+    while (mask) {
+        const int u0 = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        if (!mask) {
+            w.open(e[u0]);
+            break;
+        }
+        const int u1 = __ffs(mask) - 1;
+        mask &= mask - 1u;
+        w.put2(e[u0], e[u1]);
+    }
+}
+
 template <int kBuildWarps>
 __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_cell(
     const float4* __restrict__ pos, const uint32_t* __restrict__ pinfo, const uint32_t* __restrict__ start,
@@ -196,16 +217,8 @@ __global__ void __launch_bounds__(kBuildWarps * 32, 24 / kBuildWarps) k_build_ce
                     const uint32_t cf = __popc(hf), cb = __popc(hb);
                     nfound += cf + cb;
                     if (wf.n + wb.n + cf + cb <= max_neibs) {
-                        while (hf) {
-                            const int u = __ffs(hf) - 1;
-                            hf &= hf - 1u;
-                            wf.put(e_s[kb32 + u]);
-                        }
-                        while (hb) {
-                            const int u = __ffs(hb) - 1;
-                            hb &= hb - 1u;
-                            wb.put(e_s[kb32 + u]);
-                        }
+                        append_hits(wf, hf, e_s + kb32);
+                        append_hits(wb, hb, e_s + kb32);
                     } else {
                         // list full: keep the first hits in candidate order, count the rest
                         uint32_t h = hf | hb;
